@@ -1,0 +1,455 @@
+#!/usr/bin/env python
+"""Benchmark of the NTT library on GB300.
+
+Workload (one step): one forward NTT over BLS12-381 F_r, n = 2^24 elements
+(512 MiB per vector, larger than the 129 MB L2, so no flush is needed),
+natural-order input in Montgomery form, uniform random elements from a seed.
+Metric: NTT Melem/s = n / time per transform.
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank runs the same
+transform on its own GPU (replicas: the transforms are independent units, no
+data-path collective); `value` is the sum over ranks computed from the slowest
+rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+IMAD_PER_MUL = 264          # 8 x 32-bit CIOS: 8 x (16 + 1 + 16) multiply-adds
+IMAD_LANES_PER_SM_CLK = 64  # 32-bit integer multiply-add issue rate per SM per clock
+METRIC = "NTT Melem/s (BLS12-381 Fr, 2^24 forward) + % int/HBM roofline"
+FIELD_R = {
+    "bls12_381_fr": 0x73EDA753299D7D483339D80809A1D80553BDA402FFFE5BFEFFFFFFFF00000001,
+    "bn254_fr": 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001,
+}
+
+
+def butterfly_mults(log_n: int) -> int:
+    """Non-trivial twiddle multiplications of a radix-2 NTT: (n/2) log n - (n - 1)."""
+    n = 1 << log_n
+    return (n // 2) * log_n - (n - 1)
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2509_22684_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_hash: str, workload: str):
+    """dram bytes per launch recorded from an ncu capture of the same kernel
+    sources (profiles/ntt_traffic.json); None if absent or stale."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ntt_traffic.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = rec.get(workload)
+    if not e or e.get("kernel_hash") != kernel_hash:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="zkntt_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(field: str, log_n: int, budget_s: float, X=None):
+    """The C oracle (as it stands) on the host cores: Melem/s of forward NTTs of
+    2^log_n, repeated until `budget_s` is spent (at least once)."""
+    from oracle import cpu
+    from oracle import field as fld
+    from workloads import uniform_elements
+    F = fld.get(field)
+    if X is None:
+        X = uniform_elements(F.r, 1 << log_n, 2024)
+    threads = cpu.threads_default()
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        cpu.ntt(F, X, threads=threads)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 50:
+            break
+    return (reps << log_n) / el / 1e6, threads, reps, el
+
+
+def timed(fn, stream, steps: int) -> float:
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def extras(zk, torch, field: str, stream, peak_imad: float, hbm_gbs: float) -> dict:
+    """Other sizes, twiddle modes, and batched vs plain (rank 0, short runs)."""
+    import numpy as np
+    from workloads import batch_jobs, uniform_elements
+    out = {}
+    F_r = FIELD_R[field]
+    sizes = {}
+    for L in (20, 22, 26):
+        X = uniform_elements(F_r, 1 << L, 3000 + L)
+        x = torch.from_numpy(X.view(np.int32)).cuda()
+        y = torch.empty_like(x)
+        with zk.Plan(field, L) as p:
+            scr = torch.empty(max(8, p.scratch_bytes() // 4), dtype=torch.int32, device="cuda")
+            f = lambda: p.execute_scratch(x, y, scr, stream=stream)
+            for _ in range(3):
+                f()
+            steps = 20 if L <= 22 else 5
+            ms = timed(f, stream, steps) / steps
+            sizes[f"2^{L}"] = {"melem_s": round((1 << L) / ms / 1e3, 1), "ms": round(ms, 4),
+                              "alu_frac": round(butterfly_mults(L) * IMAD_PER_MUL / (ms / 1e3) / peak_imad, 4),
+                              "hbm_frac": round(64 * (1 << L) / (ms / 1e3) / (hbm_gbs * 1e9), 4),
+                              "digits": p.describe()["digits"]}
+        del x, y, scr
+    out["sizes"] = sizes
+    # twiddle modes at 2^24
+    L = 24
+    X = uniform_elements(F_r, 1 << L, 3024)
+    x = torch.from_numpy(X.view(np.int32)).cuda()
+    y = torch.empty_like(x)
+    modes = {}
+    for mode in ("precomp", "otf"):
+        with zk.Plan(field, L, twiddle_mode=mode) as p:
+            scr = torch.empty(p.scratch_bytes() // 4, dtype=torch.int32, device="cuda")
+            f = lambda: p.execute_scratch(x, y, scr, stream=stream)
+            for _ in range(3):
+                f()
+            ms = timed(f, stream, 10) / 10
+            modes[mode] = {"melem_s": round((1 << L) / ms / 1e3, 1), "ms": round(ms, 4),
+                           "table_mib": round(p.describe()["table_bytes"] / 2**20, 1)}
+    out["twiddle_modes_2^24"] = modes
+    del x, y
+    # Groth16 H at 2^22: seven transforms + pointwise as separate launches vs one fused launch
+    L = 22
+    a, b, c = (torch.from_numpy(uniform_elements(F_r, 1 << L, s).view(np.int32)).cuda()
+               for s in (3001, 3002, 3003))
+    h = torch.empty_like(a)
+    scr = torch.empty((3 << L, 8), dtype=torch.int32, device="cuda")
+    g16 = {}
+    for fused in (False, True):
+        f = lambda: zk.groth16_h(field, L, a, b, c, h=h, scratch=scr, fused=fused, stream=stream)
+        for _ in range(3):
+            f()
+        ms = timed(f, stream, 10) / 10
+        g16["fused_ms" if fused else "separate_ms"] = round(ms, 4)
+    g16["speedup"] = round(g16["separate_ms"] / g16["fused_ms"], 3)
+    out["groth16_2^22"] = g16
+    del a, b, c, h, scr
+    # 64 uneven transforms: persistent batch vs one call per transform
+    jobs = batch_jobs(4000, count=64, lmin=10, lmax=20)
+    plans, xs, ys = [], [], []
+    for j in jobs:
+        X = uniform_elements(FIELD_R[j.field], 1 << j.log_n, j.seed)
+        xs.append(torch.from_numpy(X.view(np.int32)).cuda())
+        ys.append(torch.empty_like(xs[-1]))
+        plans.append(zk.Plan(j.field, j.log_n, inverse=(j.kind == "intt")))
+    scr = [torch.empty(max(8, p.scratch_bytes() // 4), dtype=torch.int32, device="cuda") for p in plans]
+
+    def one_by_one():
+        for p, x, y, s in zip(plans, xs, ys, scr):
+            p.execute_scratch(x, y, s, stream=stream)
+
+    def persistent():
+        zk.execute_batch(plans, xs, ys, stream=stream)
+    bt = {}
+    for name, f in (("separate_ms", one_by_one), ("persistent_ms", persistent)):
+        for _ in range(3):
+            f()
+        bt[name] = round(timed(f, stream, 10) / 10, 4)
+    bt["elements"] = sum(1 << j.log_n for j in jobs)
+    bt["speedup"] = round(bt["separate_ms"] / bt["persistent_ms"], 3)
+    out["batch64_uneven"] = bt
+    for p in plans:
+        p.close()
+    return out
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2509_22684_gb300 as zk
+    from workloads import uniform_elements
+
+    field, L = args.field, args.log_n
+    n = 1 << L
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = measured_peaks()
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_imad = sms * IMAD_LANES_PER_SM_CLK * sm_max_mhz * 1e6
+    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
+    stream = torch.cuda.current_stream()
+
+    X = uniform_elements(FIELD_R[field], n, 2024 + rank)
+    x = torch.from_numpy(X.view(np.int32)).cuda()
+    y = torch.empty_like(x)
+    plan = zk.Plan(field, L)
+    desc = plan.describe()
+    scratch = torch.empty(plan.scratch_bytes() // 4, dtype=torch.int32, device="cuda")
+    step = lambda: plan.execute_scratch(x, y, scratch, stream=stream)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("ZKNTT_SMI_INDEX", local)))
+    clocks.start()
+    ms_total = timed(step, stream, args.steps)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    ms_max = max_over_ranks(world, ms_total)
+    zk.sync_status(stream)
+
+    # end to end through the host-buffer entry point: pinned host input,
+    # H2D + transform + D2H inside the timed region
+    xh = torch.from_numpy(X.view(np.int32)).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    e2e_step = lambda: plan.execute_host(xh, yh, stream=stream)
+    for _ in range(max(1, min(args.warmup, 3))):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_steps = max(1, min(args.steps, 10))
+    ms_e2e = max_over_ranks(world, timed(e2e_step, stream, e2e_steps))
+    ok = bool(np.array_equal(yh.numpy().view(np.uint32), y.cpu().numpy().view(np.uint32)))
+
+    passes = desc["passes"]
+    avg_launch_s = ms_total / 1e3 / (args.steps * passes)
+    alg_imad_per_launch = butterfly_mults(L) * IMAD_PER_MUL / passes
+    achieved = alg_imad_per_launch / avg_launch_s
+    value = world * n * args.steps / (ms_max / 1e3) / 1e6
+    workload = f"{field} forward NTT n=2^{L}"
+    khash = kernel_source_hash()
+    traffic = recorded_traffic(khash, workload)
+    result = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "Melem/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32 (8x32-bit limb Montgomery F_r, exact)",
+        "data": "synthetic (SplitMix64 uniform field elements, seed 2024+rank)",
+        "config": {"workload": workload, "field": field, "log_n": L, "direction": "forward",
+                   "passes": passes, "digits": desc["digits"], "twiddle_mode": desc["twiddle_mode"],
+                   "l2": "inputs larger than L2 (512 MiB per vector vs 129 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": round(achieved / 1e12, 3),
+                     "peak": round(peak_imad / 1e12, 3), "unit": "TIMAD/s",
+                     "frac": round(achieved / peak_imad, 4),
+                     "traffic": traffic,
+                     "kernel": "ntt_pass_kernel (all passes of one transform)",
+                     "peak_source": f"derived: {sms} SMs x {IMAD_LANES_PER_SM_CLK} IMAD/clk x {sm_max_mhz:.0f} MHz",
+                     "hbm_frac": round(64 * n / (ms_max / args.steps / 1e3) / (hbm_gbs * 1e9), 4),
+                     "hbm_peak_gbs": hbm_gbs},
+        "e2e": {"value": round(world * n * e2e_steps / (ms_e2e / 1e3) / 1e6, 2), "unit": "Melem/s",
+                "h2d_bytes_per_step": 32 * n, "d2h_bytes_per_step": 32 * n,
+                "api": "zkntt_execute_host (pinned host buffers)", "matches_device_result": ok},
+        "gpu_launches": args.steps * passes,
+        "clocks": clk,
+    }
+    plan.close()
+    del x, y, scratch
+    if rank == 0 and not args.no_cpu:
+        rate, cores, reps, el = cpu_oracle_rate(field, L, args.cpu_budget, X)
+        result["cpu_baseline"] = {"value": round(rate, 3), "unit": "Melem/s", "cores": cores,
+                                  "kind": "oracle",
+                                  "sample": f"C oracle (oracle/cpu_ntt.c) forward NTT 2^{L}, {reps} run(s), {el:.1f} s"}
+    if rank == 0 and not args.no_extras:
+        result["extras"] = extras(zk, torch, field, stream, peak_imad, hbm_gbs)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands, timed on the host cores: each step is one
+    forward transform of the same workload (a smaller size if the full one
+    would not finish the run within a few minutes)."""
+    if rank != 0:
+        return
+    from oracle import cpu
+    from oracle import field as fld
+    from workloads import uniform_elements
+    field = args.field
+    F = fld.get(field)
+    L = args.log_n
+    # one probe run sizes the sample
+    X = uniform_elements(F.r, 1 << L, 2024)
+    threads = cpu.threads_default()
+    t0 = time.perf_counter()
+    cpu.ntt(F, X, threads=threads)
+    per = time.perf_counter() - t0
+    total_runs = args.steps + args.warmup
+    while per * total_runs > 180 and L > 16:
+        L -= 2
+        per /= 4.4
+    if L != args.log_n:
+        X = uniform_elements(F.r, 1 << L, 2024)
+    for _ in range(args.warmup):
+        cpu.ntt(F, X, threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu.ntt(F, X, threads=threads)
+    el = time.perf_counter() - t0
+    value = (args.steps << L) / el / 1e6
+    sample = f"C oracle forward NTT 2^{L} per step on {threads} host threads"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Melem/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64 limbs (exact)",
+        "data": "synthetic", "config": {"workload": f"{field} forward NTT n=2^{args.log_n}",
+                                        "sample_log_n": L},
+        "cpu_baseline": {"value": round(value, 3), "unit": "Melem/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "Melem/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--field", default="bls12_381_fr", choices=sorted(FIELD_R))
+    ap.add_argument("--log-n", type=int, default=24)
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, world, rank)
+        return
+    world, rank, local = dist_init(args)
+    try:
+        run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

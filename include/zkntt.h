@@ -1,0 +1,227 @@
+/*
+ * zkntt.h -- C ABI of the GB300 (sm_103a) number-theoretic transform library.
+ *
+ * The transform (arxiv 2509.22684, Section II-B): for a vector a_0..a_{n-1} of
+ * elements of a prime field F_r and a primitive n-th root of unity w,
+ *     A_k = sum_{j=0}^{n-1} a_j * w^(j*k)        (k = 0..n-1, n = 2^log_n).
+ * The inverse uses w^-1 and multiplies by n^-1, so inverse(forward(a)) = a
+ * (the paper treats NTT and INTT as the same computation, Section II-B).
+ * A coset transform with shift g (Groth16 prover, Fig. 2) is
+ *     forward:  A_k = sum_j (a_j g^j) w^(jk)
+ *     inverse:  a_j = g^-j * n^-1 * sum_k A_k w^(-jk).
+ * w = w_max^(2^(s - log_n)) where w_max = g0^((r-1)/2^s), g0 the field's
+ * multiplicative generator (7 for BLS12-381 F_r, 5 for BN254 F_r) and s the
+ * 2-adicity of r - 1 (32 and 28).
+ *
+ * Element layout (Section II: field elements as word-sized limbs): 8 x uint32
+ * little-endian limbs = 32 bytes, Montgomery form X = x * 2^256 mod r,
+ * canonical (0 <= X < r).  A vector is n such elements, contiguous, natural
+ * order, 32-byte aligned.  Outputs are canonical Montgomery form too.
+ *
+ * Pointers named d_* are CUDA device pointers owned by the caller.  `stream`
+ * is a cudaStream_t passed as void* (NULL = legacy default stream).  Every
+ * execute call is stream-ordered and asynchronous: it returns once the work is
+ * enqueued.  Errors the host can see (bad arguments, launch failures) are
+ * returned at once; a device-side timeout of the persistent batch kernel is
+ * returned by zkntt_sync_status() or by the next zkntt_execute_batch() on the
+ * same context.  Plans are immutable after creation: one plan may be executed
+ * from several host threads and streams at once.
+ */
+#ifndef ZKNTT_H
+#define ZKNTT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { ZKNTT_BLS12_381_FR = 0, ZKNTT_BN254_FR = 1 } zkntt_field;
+typedef enum { ZKNTT_FORWARD = 0, ZKNTT_INVERSE = 1 } zkntt_dir;
+typedef enum {
+    ZKNTT_OK = 0,
+    ZKNTT_EINVAL = 1,        /* bad argument: null/misaligned pointer, log_n out of range, ... */
+    ZKNTT_ENOMEM = 2,        /* device allocation failed */
+    ZKNTT_ECUDA = 3,         /* a CUDA runtime call failed; see zkntt_last_cuda_error */
+    ZKNTT_ETIMEOUT = 4,      /* a bounded device-side wait gave up (batch dependency never met) */
+    ZKNTT_EUNSUPPORTED = 5   /* valid request this build does not implement */
+} zkntt_status;
+
+typedef enum {
+    ZKNTT_TWIDDLE_AUTO = 0,     /* planner / tuner decides */
+    ZKNTT_TWIDDLE_PRECOMP = 1,  /* full inter-pass twiddle tables resident in HBM */
+    ZKNTT_TWIDDLE_OTF = 2       /* small split-exponent tables, twiddles formed in registers */
+} zkntt_twiddle_mode;
+
+typedef struct zkntt_plan_s *zkntt_plan;
+
+/* One transform of a batch: input and output device vectors of the plan's size. */
+typedef struct {
+    const void *d_in;
+    void *d_out;
+} zkntt_io;
+
+/* Optional planner overrides (zero-initialise and set what you need). */
+typedef struct {
+    int twiddle_mode;      /* zkntt_twiddle_mode */
+    int num_passes;        /* 0 = planner's choice; else 1..4 */
+    int digit_bits[4];     /* log2 sub-transform size per pass, top digit first; sum = log_n */
+    int cols_per_cta[4];   /* columns per thread block per pass (1,2,4,8); 0 = planner's choice */
+    int use_tuner;         /* 1 = consult the tuning cache (ZKNTT_TUNE_CACHE) */
+} zkntt_plan_options;
+
+/*
+ * Create a plan for one transform size/direction on the current CUDA device.
+ *   out          receives the plan handle (not written on failure)
+ *   field        ZKNTT_BLS12_381_FR or ZKNTT_BN254_FR
+ *   log_n        1 .. 28 for both fields (device-memory bound; the fields'
+ *                2-adicities are 32 and 28)
+ *   dir          ZKNTT_FORWARD or ZKNTT_INVERSE
+ *   coset_shift  NULL for a plain transform, else the shift g as 8 uint32
+ *                Montgomery-form limbs (host memory, read during the call);
+ *                must be nonzero and canonical.
+ * The plan owns its device twiddle tables (allocated and filled here, freed by
+ * zkntt_plan_destroy).  Returns EINVAL on bad arguments, ENOMEM when the tables
+ * do not fit, ECUDA on other CUDA failures.
+ */
+zkntt_status zkntt_plan_create(zkntt_plan *out, zkntt_field field, int log_n, zkntt_dir dir,
+                               const uint32_t *coset_shift);
+
+/* As zkntt_plan_create, with planner overrides (opts may be NULL). */
+zkntt_status zkntt_plan_create_ex(zkntt_plan *out, zkntt_field field, int log_n, zkntt_dir dir,
+                                  const uint32_t *coset_shift, const zkntt_plan_options *opts);
+
+/* Free the plan's device tables.  The caller must ensure no work using the
+ * plan is still in flight.  NULL is accepted. */
+zkntt_status zkntt_plan_destroy(zkntt_plan plan);
+
+/* Size in bytes of the scratch vector an execution of this plan needs
+ * (0 for single-pass sizes, else n * 32). */
+zkntt_status zkntt_plan_scratch_bytes(zkntt_plan plan, size_t *bytes);
+
+/* Describe the plan: number of passes, digit bits per pass, twiddle mode and
+ * the bytes of device tables it holds (any pointer may be NULL). */
+zkntt_status zkntt_plan_describe(zkntt_plan plan, int *num_passes, int digit_bits[4],
+                                 int *twiddle_mode, size_t *table_bytes);
+
+/*
+ * Run one transform: d_out = T(d_in), n = 2^log_n elements each.
+ * d_in == d_out (in place) is allowed; partial overlap is EINVAL.  Scratch for
+ * multi-pass sizes comes from the device's stream-ordered memory pool
+ * (cudaMallocAsync on `stream`, released on `stream`).
+ */
+zkntt_status zkntt_execute(zkntt_plan plan, const void *d_in, void *d_out, void *stream);
+
+/* As zkntt_execute with caller-owned scratch (at least zkntt_plan_scratch_bytes
+ * bytes, 32-byte aligned, not overlapping d_in/d_out); allocates nothing. */
+zkntt_status zkntt_execute_scratch(zkntt_plan plan, const void *d_in, void *d_out,
+                                   void *d_scratch, size_t scratch_bytes, void *stream);
+
+/*
+ * End-to-end form for callers holding the data in HOST memory: copies h_in
+ * (n elements) to the device, runs the transform and copies the result to
+ * h_out, all ordered on `stream` (device buffers come from the stream-ordered
+ * pool and are released on the stream).  Returns once enqueued; h_out is valid
+ * after the stream synchronises.  Pinned (page-locked) host buffers give
+ * asynchronous copies; pageable ones are staged by the CUDA runtime.
+ */
+zkntt_status zkntt_execute_host(zkntt_plan plan, const void *h_in, void *h_out, void *stream);
+
+/*
+ * Run `count` independent transforms (each with its own plan; sizes, fields and
+ * directions may differ) as ONE persistent kernel launch.  Work items (job,
+ * pass, tile) are pulled from a device queue; a job's pass starts once all its
+ * previous pass's tiles are done (bounded spin; on expiry the launch sets an
+ * error word and returns, reported as ETIMEOUT).  ptrs[i] gives job i's
+ * vectors.  In-place jobs are allowed; different jobs must not overlap.
+ * Job scratch comes from the stream-ordered pool.
+ */
+zkntt_status zkntt_execute_batch(const zkntt_plan *plans, const zkntt_io *ptrs, int count,
+                                 void *stream);
+
+/*
+ * Groth16 H polynomial (Fig. 2; Section IV-A: seven NTT operations):
+ *   a' = iNTT(a), b' = iNTT(b), c' = iNTT(c);
+ *   A = cosetNTT_g(a'), B = cosetNTT_g(b'), C = cosetNTT_g(c');
+ *   H_i = (A_i B_i - C_i) * (g^n - 1)^-1     (Z(x) = x^n - 1 on the coset g*w^i)
+ *   d_h = cosetINTT_g(H)
+ * with g the field's multiplicative generator.  d_a, d_b, d_c, d_h: n elements
+ * each (inputs are read only).  d_scratch: 3 * n * 32 bytes of caller-owned
+ * device memory.  fused = 1 runs the whole sequence as one persistent launch
+ * (pointwise fused into the last transform's first pass); fused = 0 issues the
+ * seven transforms and the pointwise kernel as separate launches.
+ */
+zkntt_status zkntt_groth16_h(zkntt_field field, int log_n, const void *d_a, const void *d_b,
+                             const void *d_c, void *d_h, void *d_scratch, int fused,
+                             void *stream);
+
+/* Static text for a status code. */
+const char *zkntt_status_str(zkntt_status status);
+
+/* The last CUDA error code this library saw on the calling thread (0 = none). */
+zkntt_status zkntt_last_cuda_error(int *err);
+
+/* Wait for `stream` and report any device-side error word (ETIMEOUT) or CUDA
+ * error raised by work this library enqueued on it. */
+zkntt_status zkntt_sync_status(void *stream);
+
+/* Fault-injection self-test of the persistent kernel's bounded wait: launches
+ * it with a single work item whose dependency can never be met (injected on
+ * the host) and a device-side wait limit of timeout_ms, then returns what
+ * zkntt_sync_status reports -- ZKNTT_ETIMEOUT when the bound works.  No GPU
+ * fault is involved; the context stays usable. */
+zkntt_status zkntt_selftest_timeout(int timeout_ms, void *stream);
+
+/* Field information: modulus and Montgomery form of the generator, 8 limbs
+ * each (host memory, either may be NULL), and the 2-adicity. */
+zkntt_status zkntt_field_info(zkntt_field field, uint32_t modulus[8], uint32_t generator_mont[8],
+                              int *two_adicity);
+
+/* Elementwise field operations on device vectors of n elements (test and
+ * calibration entry points for the butterfly arithmetic):
+ *   op 0: c = a * b (Montgomery product a b 2^-256 mod r)
+ *   op 1: c = a + b mod r      op 2: c = a - b mod r
+ */
+zkntt_status zkntt_field_op(zkntt_field field, int op, const void *d_a, const void *d_b, void *d_c,
+                            size_t n, void *stream);
+
+/* Groth16 pointwise step on its own: d_h_i = (a_i b_i - c_i) * z, z given as
+ * 8 Montgomery limbs in host memory. */
+zkntt_status zkntt_pointwise(zkntt_field field, const void *d_a, const void *d_b, const void *d_c,
+                             const uint32_t *z_mont, void *d_h, size_t n, void *stream);
+
+/* Result of zkntt_tune: the fastest schedule found. */
+typedef struct {
+    int num_passes;
+    int digit_bits[4];
+    int cols_per_cta[4];
+    int twiddle_mode;
+    float ms;            /* median time of one transform with that schedule */
+} zkntt_tune_result;
+
+/*
+ * Autotuner (the paper's call for runtime parameter tuning, Section V-A): time
+ * up to `max_candidates` schedules (pass split, columns per block, twiddle
+ * mode) for one plain transform of 2^log_n elements on the current device with
+ * CUDA events, remember the fastest for this GPU (and append it to the file
+ * named by ZKNTT_TUNE_CACHE, one JSON object per line) and return it in *best
+ * (may be NULL).  Plans created with opts->use_tuner = 1 then use it.  Uses
+ * 3 * n * 32 bytes of temporary device memory; synchronous.
+ */
+zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_candidates,
+                        zkntt_tune_result *best);
+
+/*
+ * Integer-pipe calibration: runs `iters` Montgomery products per thread on a
+ * grid of `blocks` x `threads` (register-resident, no memory traffic inside
+ * the loop) and writes one checksum word per thread to d_sink.  Used to
+ * measure the sustained 32-bit multiply-add rate that bounds the transform.
+ */
+zkntt_status zkntt_mulbench(zkntt_field field, int blocks, int threads, int iters, void *d_sink,
+                            void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZKNTT_H */

@@ -1,0 +1,118 @@
+// aux_kernels.cuh -- table generation, elementwise field kernels and the
+// integer-pipe calibration kernel.
+#pragma once
+#include <cstdint>
+
+#include "field.cuh"
+#include "ntt_pass.cuh"
+
+namespace zkntt {
+
+// out[i] = hi[i >> split] * lo[i & (2^split - 1)]: the powers b^i from two
+// small tables (b^(i_hi * 2^split) and b^i_lo)
+template <class F>
+__global__ void gen_powers_kernel(uint4 *out, uint32_t count, const uint4 *hi, const uint4 *lo,
+                                  uint32_t split) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        uint32_t a[8], b[8];
+        ldg_elem(a, hi + 2 * size_t(i >> split));
+        ldg_elem(b, lo + 2 * size_t(i & ((1u << split) - 1u)));
+        mul<F>(a, a, b);
+        st_elem(out + 2 * size_t(i), a);
+    }
+}
+
+// Inter-pass twiddle table in position order:
+//   out[lo * 2^K + d] = w^(lo * rev_K(d)) * fl[lo] * fd[d]
+// with w^e = w_hi[e >> split] * w_lo[e & mask] (any scalar factor folded into
+// w_lo by the host).  fl / fd may be null.
+template <class F>
+__global__ void gen_twiddle_kernel(uint4 *out, uint32_t K, uint32_t lo_bits, const uint4 *w_hi,
+                                   const uint4 *w_lo, uint32_t split, const uint4 *fl,
+                                   const uint4 *fd) {
+    const size_t total = size_t(1) << (lo_bits + K);
+    for (size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+         idx += size_t(gridDim.x) * blockDim.x) {
+        uint32_t lo = uint32_t(idx >> K);
+        uint32_t d = uint32_t(idx & ((size_t(1) << K) - 1));
+        uint32_t e = lo * brev_bits(d, K);  // < 2^(lo_bits + K)
+        uint32_t a[8], b[8];
+        ldg_elem(a, w_hi + 2 * size_t(e >> split));
+        ldg_elem(b, w_lo + 2 * size_t(e & ((1u << split) - 1u)));
+        mul<F>(a, a, b);
+        if (fl) {
+            ldg_elem(b, fl + 2 * size_t(lo));
+            mul<F>(a, a, b);
+        }
+        if (fd) {
+            ldg_elem(b, fd + 2 * size_t(d));
+            mul<F>(a, a, b);
+        }
+        st_elem(out + 2 * idx, a);
+    }
+}
+
+// c = op(a, b) elementwise: 0 mul, 1 add, 2 sub
+template <class F>
+__global__ void field_op_kernel(int op, const uint4 *a, const uint4 *b, uint4 *c, size_t n) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += size_t(gridDim.x) * blockDim.x) {
+        uint32_t x[8], y[8], z[8];
+        ldg_elem(x, a + 2 * i);
+        ldg_elem(y, b + 2 * i);
+        if (op == 0) mul<F>(z, x, y);
+        else if (op == 1) add<F>(z, x, y);
+        else sub<F>(z, x, y);
+        st_elem(c + 2 * i, z);
+    }
+}
+
+// Groth16 pointwise on the coset: h = (a * b - c) * z
+template <class F>
+__global__ void pointwise_kernel(const uint4 *a, const uint4 *b, const uint4 *c, const uint4 *z,
+                                 uint4 *h, size_t n) {
+    uint32_t zz[8];
+    ldg_elem(zz, z);
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += size_t(gridDim.x) * blockDim.x) {
+        uint32_t x[8], y[8], w[8];
+        ldg_elem(x, a + 2 * i);
+        ldg_elem(y, b + 2 * i);
+        mul<F>(x, x, y);
+        ldg_elem(w, c + 2 * i);
+        sub<F>(x, x, w);
+        mul<F>(x, x, zz);
+        st_elem(h + 2 * i, x);
+    }
+}
+
+// Calibration: four independent chains of Montgomery products per thread, all
+// in registers; one checksum word per thread keeps the work live.
+template <class F>
+__global__ void __launch_bounds__(256) mulbench_kernel(int iters, uint32_t *sink) {
+    uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t x0[8], x1[8], x2[8], x3[8], y[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        // small distinct canonical values (top limb cleared keeps them below r)
+        uint32_t v = tid * 0x9E3779B9u + j * 0x85EBCA6Bu;
+        x0[j] = v;
+        x1[j] = v ^ 0x5bd1e995u;
+        x2[j] = v + 0x27d4eb2fu;
+        x3[j] = v * 3u + 1u;
+        y[j] = v ^ 0xc2b2ae35u;
+    }
+    x0[7] = x1[7] = x2[7] = x3[7] = y[7] = 0;
+    for (int it = 0; it < iters; it++) {
+        mul<F>(x0, x0, y);
+        mul<F>(x1, x1, y);
+        mul<F>(x2, x2, y);
+        mul<F>(x3, x3, y);
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) acc ^= x0[j] ^ x1[j] ^ x2[j] ^ x3[j];
+    sink[tid] = acc;
+}
+
+}  // namespace zkntt

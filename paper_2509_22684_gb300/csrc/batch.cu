@@ -1,0 +1,102 @@
+// batch.cu -- the persistent batch kernel (both fields, every digit size).
+#include "batch.cuh"
+#include "kernels.h"
+
+namespace zkntt {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// One out-of-line tile routine per (field, digit size): the persistent kernel
+// calls it through a switch, so each body is register-allocated on its own.
+template <class F, int K>
+__device__ __noinline__ void batch_tile(const PassArgs &a, uint4 *smem, uint32_t tile) {
+    run_tile<F, K>(a, smem, tile);
+}
+
+template <class F>
+__device__ __forceinline__ void run_tile_k(const PassArgs &a, uint4 *smem, uint32_t K,
+                                           uint32_t tile) {
+    switch (K) {
+        case 1: batch_tile<F, 1>(a, smem, tile); break;
+        case 2: batch_tile<F, 2>(a, smem, tile); break;
+        case 3: batch_tile<F, 3>(a, smem, tile); break;
+        case 4: batch_tile<F, 4>(a, smem, tile); break;
+        case 5: batch_tile<F, 5>(a, smem, tile); break;
+        case 6: batch_tile<F, 6>(a, smem, tile); break;
+        case 7: batch_tile<F, 7>(a, smem, tile); break;
+        case 8: batch_tile<F, 8>(a, smem, tile); break;
+        case 9: batch_tile<F, 9>(a, smem, tile); break;
+        case 10: batch_tile<F, 10>(a, smem, tile); break;
+        default: batch_tile<F, 11>(a, smem, tile); break;
+    }
+}
+
+// ctrl[0]: next work item, ctrl[1]: abort word; done[s]: tiles retired per
+// segment; status: sticky per-device error word read by the host.
+__global__ void __launch_bounds__(BATCH_THREADS, 2)
+    batch_kernel(const __grid_constant__ BatchTable tab, uint32_t *ctrl, uint32_t *done,
+                 uint32_t *status) {
+    extern __shared__ uint4 smem[];
+    __shared__ uint32_t s_item, s_seg, s_stop;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t stop = 0, segi = 0;
+            uint32_t item = atomicAdd(&ctrl[0], 1u);
+            if (item >= tab.total_items || *(volatile uint32_t *)&ctrl[1]) {
+                stop = 1;
+            } else {
+                uint32_t lo = 0, hi = tab.nseg;  // last segment with first_item <= item
+                while (hi - lo > 1) {
+                    uint32_t mid = (lo + hi) >> 1;
+                    if (tab.seg[mid].first_item <= item) lo = mid;
+                    else hi = mid;
+                }
+                segi = lo;
+                const BatchSeg &sg = tab.seg[segi];
+                for (int k = 0; k < 3 && !stop; k++) {
+                    if (sg.dep[k] < 0) continue;
+                    const uint32_t *cnt = done + sg.dep[k];
+                    unsigned long long t0 = global_ns();
+                    while (ld_acquire(cnt) < sg.dep_tiles[k]) {
+                        if (*(volatile uint32_t *)&ctrl[1]) { stop = 1; break; }
+                        if (global_ns() - t0 > tab.timeout_ns) {
+                            atomicExch(&ctrl[1], 1u);
+                            atomicOr(status, BATCH_STATUS_TIMEOUT);
+                            stop = 1;
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                }
+            }
+            s_item = item;
+            s_seg = segi;
+            s_stop = stop;
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const BatchSeg &sg = tab.seg[s_seg];
+        const uint32_t tile = s_item - sg.first_item;
+        if (sg.field == 0) run_tile_k<FrBLS12_381>(sg.a, smem, sg.K, tile);
+        else run_tile_k<FrBN254>(sg.a, smem, sg.K, tile);
+        // run_tile ends with a block barrier: every store of the tile is issued
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&done[s_seg], 1u);
+        }
+    }
+}
+
+const void *batch_kernel_ptr() { return (const void *)&batch_kernel; }
+
+}  // namespace zkntt

@@ -1,0 +1,51 @@
+// batch.cuh -- persistent kernel running many transforms (uneven sizes, both
+// fields, with dependencies between them) in one launch.
+//
+// The paper finds that the Groth16 prover issues "seven NTT operations, each
+// with multiple kernel launches" (Section IV-A) and that such short kernels run
+// with sub-optimal launch parameters; it calls for runtime autotuning (Section
+// V-A).  Here every pass of every transform is a segment of tiles; all tiles of
+// all segments form one work list ordered by dependency level.  Resident
+// blocks (one grid sized to the SM count) pull the next tile index from a
+// device counter.  A segment may depend on up to three earlier segments (the
+// previous pass of the same transform, or the producers of its input); the
+// block that claims a tile waits until those segments have retired all their
+// tiles.  Because tiles are claimed in list order and every dependency points
+// to an earlier position, the oldest unfinished tile can always run, so the
+// scheme cannot deadlock however many blocks are resident.
+//
+// Every wait is bounded by `timeout_ns` (device global timer).  On expiry the
+// block sets the launch's abort word and the sticky status word, and all blocks
+// leave; the host reports ZKNTT_ETIMEOUT.
+#pragma once
+#include <cstdint>
+
+#include "field.cuh"
+#include "ntt_pass.cuh"
+
+namespace zkntt {
+
+constexpr int BATCH_MAX_SEGMENTS = 160;
+constexpr uint32_t BATCH_THREADS = 256;
+constexpr uint32_t BATCH_STATUS_TIMEOUT = 4u;  // == ZKNTT_ETIMEOUT
+
+struct BatchSeg {
+    PassArgs a;
+    uint32_t field;       // 0 BLS12-381 F_r, 1 BN254 F_r
+    uint32_t K;           // digit bits of this pass
+    uint32_t first_item;  // index of the segment's first tile in the work list
+    int32_t dep[3];       // segments that must be complete first (-1: none)
+    uint32_t dep_tiles[3];
+};
+
+struct BatchTable {
+    uint32_t nseg;
+    uint32_t total_items;
+    unsigned long long timeout_ns;
+    BatchSeg seg[BATCH_MAX_SEGMENTS];
+};
+
+// passed by value as a kernel parameter (limit 32764 bytes)
+static_assert(sizeof(BatchTable) <= 32000, "batch table exceeds the kernel parameter limit");
+
+}  // namespace zkntt

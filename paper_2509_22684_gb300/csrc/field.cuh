@@ -1,0 +1,260 @@
+// field.cuh -- prime-field arithmetic on 8 x 32-bit limbs for sm_103a.
+//
+// Elements are 256-bit little-endian limb vectors in Montgomery form
+// (X = x * 2^256 mod r), as the paper describes field elements: word-sized
+// limbs (Section II), results of every field operation in [0, r).
+//
+// * mul: Montgomery product X * Y * 2^-256 mod r, coarsely integrated operand
+//   scanning (CIOS): for each limb b_i, t += a * b_i, then m = t_0 * r' and
+//   t = (t + m * r) / 2^32.  The paper finds FF_mul to be the dominant cost of
+//   the NTT (Section IV-B: FF_mul + FF_sqr are 93.8% of NTT time) and the
+//   32-bit multiply-add (IMAD) the dominant instruction (Section IV-B-2).  Each
+//   carry chain below is a single asm statement of mad.lo.cc / madc.hi.cc
+//   instructions, so the carry flag never has to survive between statements.
+//   For r < 2^255 (both fields here) the running value t stays below 2r after
+//   each outer step, so nine limbs suffice and no tenth carry limb is kept.
+// * add / sub: the paper measures the conditional-reduction branches as 70.5%
+//   of FF_add latency (Section IV-B-1) and 52-56% branch efficiency (Section
+//   IV-C).  Here both candidates are computed and one is selected with a mask
+//   from the borrow -- no branch.
+//
+// Field-specific shortcut: BLS12-381 F_r has r = 1 mod 2^32, i.e. limb 0 of r
+// is 1 and r' = -r^-1 mod 2^32 = 2^32 - 1.  Then m = -t_0 and t_0 + m * r_0 is
+// 0 with carry (t_0 != 0), and hi(m * r_0) = 0: three multiplies per outer step
+// become one add (240 instead of 264 multiply-adds per product).
+#pragma once
+#include <cstdint>
+
+namespace zkntt {
+
+struct FrBLS12_381 {
+    static constexpr uint32_t P0 = 0x00000001u, P1 = 0xffffffffu, P2 = 0xfffe5bfeu, P3 = 0x53bda402u,
+                              P4 = 0x09a1d805u, P5 = 0x3339d808u, P6 = 0x299d7d48u, P7 = 0x73eda753u;
+    static constexpr uint32_t RP = 0xffffffffu;  // -r^-1 mod 2^32
+    static constexpr bool P0_IS_ONE = true;
+    static constexpr int ID = 0;
+};
+
+struct FrBN254 {
+    static constexpr uint32_t P0 = 0xf0000001u, P1 = 0x43e1f593u, P2 = 0x79b97091u, P3 = 0x2833e848u,
+                              P4 = 0x8181585du, P5 = 0xb85045b6u, P6 = 0xe131a029u, P7 = 0x30644e72u;
+    static constexpr uint32_t RP = 0xefffffffu;
+    static constexpr bool P0_IS_ONE = false;
+    static constexpr int ID = 1;
+};
+
+// ---------------------------------------------------------------------------
+// conditional subtraction of r: x in [0, 2r) -> [0, r), branch-free
+template <class F>
+__device__ __forceinline__ void reduce_once(uint32_t x[8]) {
+    uint32_t u[8], mask;
+    asm("sub.cc.u32  %0, %9, %17;\n\t"
+        "subc.cc.u32 %1, %10, %18;\n\t"
+        "subc.cc.u32 %2, %11, %19;\n\t"
+        "subc.cc.u32 %3, %12, %20;\n\t"
+        "subc.cc.u32 %4, %13, %21;\n\t"
+        "subc.cc.u32 %5, %14, %22;\n\t"
+        "subc.cc.u32 %6, %15, %23;\n\t"
+        "subc.cc.u32 %7, %16, %24;\n\t"
+        "subc.u32    %8, 0, 0;"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+          "=r"(u[7]), "=r"(mask)
+        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(x[7]),
+          "n"(F::P0), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5), "n"(F::P6),
+          "n"(F::P7));
+    // mask = all ones when x < r (borrow): keep x, else take x - r
+#pragma unroll
+    for (int i = 0; i < 8; i++) x[i] = u[i] ^ ((x[i] ^ u[i]) & mask);
+}
+
+// r = a + b mod p, inputs canonical
+template <class F>
+__device__ __forceinline__ void add(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
+    asm("add.cc.u32  %0, %8, %16;\n\t"
+        "addc.cc.u32 %1, %9, %17;\n\t"
+        "addc.cc.u32 %2, %10, %18;\n\t"
+        "addc.cc.u32 %3, %11, %19;\n\t"
+        "addc.cc.u32 %4, %12, %20;\n\t"
+        "addc.cc.u32 %5, %13, %21;\n\t"
+        "addc.cc.u32 %6, %14, %22;\n\t"
+        "addc.u32    %7, %15, %23;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
+          "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
+    reduce_once<F>(r);  // a + b < 2r < 2^256: no carry out of limb 7
+}
+
+// r = a - b mod p, inputs canonical
+template <class F>
+__device__ __forceinline__ void sub(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
+    uint32_t mask;
+    asm("sub.cc.u32  %0, %9, %17;\n\t"
+        "subc.cc.u32 %1, %10, %18;\n\t"
+        "subc.cc.u32 %2, %11, %19;\n\t"
+        "subc.cc.u32 %3, %12, %20;\n\t"
+        "subc.cc.u32 %4, %13, %21;\n\t"
+        "subc.cc.u32 %5, %14, %22;\n\t"
+        "subc.cc.u32 %6, %15, %23;\n\t"
+        "subc.cc.u32 %7, %16, %24;\n\t"
+        "subc.u32    %8, 0, 0;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(mask)
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
+          "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
+    // on borrow add r back (mask selects the modulus limbs)
+    asm("add.cc.u32  %0, %0, %8;\n\t"
+        "addc.cc.u32 %1, %1, %9;\n\t"
+        "addc.cc.u32 %2, %2, %10;\n\t"
+        "addc.cc.u32 %3, %3, %11;\n\t"
+        "addc.cc.u32 %4, %4, %12;\n\t"
+        "addc.cc.u32 %5, %5, %13;\n\t"
+        "addc.cc.u32 %6, %6, %14;\n\t"
+        "addc.u32    %7, %7, %15;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+          "+r"(r[7])
+        : "r"(F::P0 & mask), "r"(F::P1 & mask), "r"(F::P2 & mask), "r"(F::P3 & mask),
+          "r"(F::P4 & mask), "r"(F::P5 & mask), "r"(F::P6 & mask), "r"(F::P7 & mask));
+}
+
+// ---------------------------------------------------------------------------
+// One CIOS outer step: t (< 2r, limbs t0..t7, t8 = 0 on entry) becomes
+// (t + a * b + m * r) / 2^32 with m = t0' * r' chosen so the division is exact.
+template <class F>
+__device__ __forceinline__ void cios_step(uint32_t t[9], const uint32_t a[8], uint32_t b) {
+    // t[0..7] += lo(a_j b); t8 = carry
+    asm("mad.lo.cc.u32  %0, %9, %17, %0;\n\t"
+        "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"
+        "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"
+        "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"
+        "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"
+        "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"
+        "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"
+        "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"
+        "addc.u32       %8, 0, 0;"
+        : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]),
+          "+r"(t[7]), "=r"(t[8])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
+          "r"(b));
+    // t[1..8] += hi(a_j b)
+    asm("mad.hi.cc.u32  %0, %8, %16, %0;\n\t"
+        "madc.hi.cc.u32 %1, %9, %16, %1;\n\t"
+        "madc.hi.cc.u32 %2, %10, %16, %2;\n\t"
+        "madc.hi.cc.u32 %3, %11, %16, %3;\n\t"
+        "madc.hi.cc.u32 %4, %12, %16, %4;\n\t"
+        "madc.hi.cc.u32 %5, %13, %16, %5;\n\t"
+        "madc.hi.cc.u32 %6, %14, %16, %6;\n\t"
+        "madc.hi.u32    %7, %15, %16, %7;"
+        : "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
+          "+r"(t[8])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
+          "r"(b));
+    if constexpr (F::P0_IS_ONE) {
+        // r' = -1: m = -t0; t0 + m * 1 = 0 with carry (t0 != 0); hi(m * 1) = 0
+        uint32_t m = 0u - t[0];
+        asm("add.cc.u32     %0, %0, %9;\n\t"
+            "madc.lo.cc.u32 %1, %9, %10, %1;\n\t"
+            "madc.lo.cc.u32 %2, %9, %11, %2;\n\t"
+            "madc.lo.cc.u32 %3, %9, %12, %3;\n\t"
+            "madc.lo.cc.u32 %4, %9, %13, %4;\n\t"
+            "madc.lo.cc.u32 %5, %9, %14, %5;\n\t"
+            "madc.lo.cc.u32 %6, %9, %15, %6;\n\t"
+            "madc.lo.cc.u32 %7, %9, %16, %7;\n\t"
+            "addc.u32       %8, %8, 0;"
+            : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]),
+              "+r"(t[7]), "+r"(t[8])
+            : "r"(m), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5), "n"(F::P6),
+              "n"(F::P7));
+        asm("mad.hi.cc.u32  %0, %7, %8, %0;\n\t"
+            "madc.hi.cc.u32 %1, %7, %9, %1;\n\t"
+            "madc.hi.cc.u32 %2, %7, %10, %2;\n\t"
+            "madc.hi.cc.u32 %3, %7, %11, %3;\n\t"
+            "madc.hi.cc.u32 %4, %7, %12, %4;\n\t"
+            "madc.hi.cc.u32 %5, %7, %13, %5;\n\t"
+            "madc.hi.u32    %6, %7, %14, %6;"
+            : "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8])
+            : "r"(m), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5), "n"(F::P6),
+              "n"(F::P7));
+    } else {
+        uint32_t m = t[0] * F::RP;
+        asm("mad.lo.cc.u32  %0, %9, %10, %0;\n\t"
+            "madc.lo.cc.u32 %1, %9, %11, %1;\n\t"
+            "madc.lo.cc.u32 %2, %9, %12, %2;\n\t"
+            "madc.lo.cc.u32 %3, %9, %13, %3;\n\t"
+            "madc.lo.cc.u32 %4, %9, %14, %4;\n\t"
+            "madc.lo.cc.u32 %5, %9, %15, %5;\n\t"
+            "madc.lo.cc.u32 %6, %9, %16, %6;\n\t"
+            "madc.lo.cc.u32 %7, %9, %17, %7;\n\t"
+            "addc.u32       %8, %8, 0;"
+            : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]),
+              "+r"(t[7]), "+r"(t[8])
+            : "r"(m), "n"(F::P0), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5),
+              "n"(F::P6), "n"(F::P7));
+        asm("mad.hi.cc.u32  %0, %8, %9, %0;\n\t"
+            "madc.hi.cc.u32 %1, %8, %10, %1;\n\t"
+            "madc.hi.cc.u32 %2, %8, %11, %2;\n\t"
+            "madc.hi.cc.u32 %3, %8, %12, %3;\n\t"
+            "madc.hi.cc.u32 %4, %8, %13, %4;\n\t"
+            "madc.hi.cc.u32 %5, %8, %14, %5;\n\t"
+            "madc.hi.cc.u32 %6, %8, %15, %6;\n\t"
+            "madc.hi.u32    %7, %8, %16, %7;"
+            : "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
+              "+r"(t[8])
+            : "r"(m), "n"(F::P0), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5),
+              "n"(F::P6), "n"(F::P7));
+    }
+    // divide by 2^32 (t0 is now 0)
+#pragma unroll
+    for (int j = 0; j < 8; j++) t[j] = t[j + 1];
+    t[8] = 0;
+}
+
+// r = a * b * 2^-256 mod p; a, b canonical; r may alias a or b
+template <class F>
+__device__ __forceinline__ void mul(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
+    uint32_t t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t bb[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) bb[i] = b[i];
+#pragma unroll
+    for (int i = 0; i < 8; i++) cios_step<F>(t, a, bb[i]);
+    reduce_once<F>(t);
+#pragma unroll
+    for (int i = 0; i < 8; i++) r[i] = t[i];
+}
+
+// Out-of-line Montgomery product for the once-per-element side paths (input
+// and output scales, on-the-fly twiddle composition): keeps the unrolled
+// kernels small; the butterfly products stay inline.
+template <class F>
+__device__ __noinline__ void mul_call(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
+    mul<F>(r, a, b);
+}
+
+// ---------------------------------------------------------------------------
+// element load/store: 32 bytes as two 16-byte vectors
+__device__ __forceinline__ void ld_elem(uint32_t x[8], const uint4 *p) {
+    uint4 lo = p[0], hi = p[1];
+    x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
+    x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
+}
+
+__device__ __forceinline__ void ldg_elem(uint32_t x[8], const uint4 *p) {
+    uint4 lo = __ldg(p), hi = __ldg(p + 1);
+    x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
+    x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
+}
+
+// L2-coherent load (bypasses L1) for data another block wrote in this launch
+__device__ __forceinline__ void ld_elem_cg(uint32_t x[8], const uint4 *p) {
+    uint4 lo = __ldcg(p), hi = __ldcg(p + 1);
+    x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
+    x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
+}
+
+__device__ __forceinline__ void st_elem(uint4 *p, const uint32_t x[8]) {
+    p[0] = make_uint4(x[0], x[1], x[2], x[3]);
+    p[1] = make_uint4(x[4], x[5], x[6], x[7]);
+}
+
+}  // namespace zkntt

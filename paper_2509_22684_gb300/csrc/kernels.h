@@ -1,0 +1,23 @@
+// kernels.h -- per-field table of kernel entry points, filled by the
+// field-specific translation units and used by the host runtime.
+#pragma once
+#include <cstdint>
+
+namespace zkntt {
+
+constexpr int MAX_DIGIT_BITS = 11;  // largest sub-transform a block holds (2^11 x 32 B = 64 KiB)
+
+struct FieldKernels {
+    const void *pass[MAX_DIGIT_BITS + 1];  // ntt_pass_kernel<F, K>, K = 1..11
+    const void *gen_powers;
+    const void *gen_twiddle;
+    const void *field_op;
+    const void *pointwise;
+    const void *mulbench;
+};
+
+const FieldKernels &kernels_bls12_381();
+const FieldKernels &kernels_bn254();
+const void *batch_kernel_ptr();
+
+}  // namespace zkntt

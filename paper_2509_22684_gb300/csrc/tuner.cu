@@ -1,0 +1,249 @@
+// tuner.cu -- the autotuner: search over pass splits, block shapes and twiddle
+// modes for one transform size, timed on the device with CUDA events.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/zkntt.h"
+#include "kernels.h"
+#include "tuner.h"
+
+namespace zkntt {
+namespace {
+
+std::mutex g_mu;
+bool g_loaded = false;
+std::map<std::tuple<std::string, int, int, int>, TuneEntry> g_cache;
+
+std::string gpu_name() {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    std::string n = prop.name;
+    for (char &c : n)
+        if (c == '"' || c == '\n') c = '_';
+    return n;
+}
+
+const char *cache_path() {
+    const char *p = getenv("ZKNTT_TUNE_CACHE");
+    return (p && *p) ? p : nullptr;
+}
+
+// one entry per line:
+// {"gpu":"NAME","field":F,"log_n":L,"dir":D,"passes":P,"digits":[a,b,c,d],"log_cols":[a,b,c,d],"mode":M,"ms":T}
+void load_locked() {
+    if (g_loaded) return;
+    g_loaded = true;
+    const char *path = cache_path();
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+        char name[256] = {0};
+        int field, L, dir;
+        TuneEntry e;
+        const char *q = strstr(line, "\"gpu\":\"");
+        if (!q) continue;
+        q += 7;
+        const char *end = strchr(q, '"');
+        if (!end || end - q >= 255) continue;
+        memcpy(name, q, end - q);
+        int n = sscanf(end + 1,
+                       ",\"field\":%d,\"log_n\":%d,\"dir\":%d,\"passes\":%d,\"digits\":[%d,%d,%d,%d],"
+                       "\"log_cols\":[%d,%d,%d,%d],\"mode\":%d,\"ms\":%lf",
+                       &field, &L, &dir, &e.passes, &e.digits[0], &e.digits[1], &e.digits[2],
+                       &e.digits[3], &e.log_cols[0], &e.log_cols[1], &e.log_cols[2], &e.log_cols[3],
+                       &e.mode, &e.ms);
+        if (n == 14) g_cache[{std::string(name), field, L, dir}] = e;
+    }
+    fclose(f);
+}
+
+}  // namespace
+
+bool tuner_lookup(int field, int log_n, int dir, TuneEntry *out) {
+    std::string name = gpu_name();
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_locked();
+    auto it = g_cache.find({name, field, log_n, dir});
+    if (it == g_cache.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+void tuner_store(int field, int log_n, int dir, const TuneEntry &e) {
+    std::string name = gpu_name();
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_locked();
+    g_cache[{name, field, log_n, dir}] = e;
+    const char *path = cache_path();
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f,
+            "{\"gpu\":\"%s\",\"field\":%d,\"log_n\":%d,\"dir\":%d,\"passes\":%d,\"digits\":[%d,%d,%d,%d],"
+            "\"log_cols\":[%d,%d,%d,%d],\"mode\":%d,\"ms\":%.6f}\n",
+            name.c_str(), field, log_n, dir, e.passes, e.digits[0], e.digits[1], e.digits[2],
+            e.digits[3], e.log_cols[0], e.log_cols[1], e.log_cols[2], e.log_cols[3], e.mode, e.ms);
+    fclose(f);
+}
+
+namespace {
+
+// digit splits of L into p parts in [lo, MAX_DIGIT_BITS], near-balanced
+void splits(int L, int p, std::vector<std::vector<int>> &out) {
+    std::vector<int> cur(p, 0);
+    std::function<void(int, int)> rec = [&](int i, int left) {
+        if (i == p - 1) {
+            if (left < 3 || left > MAX_DIGIT_BITS) return;
+            cur[i] = left;
+            int mx = *std::max_element(cur.begin(), cur.end());
+            int mn = *std::min_element(cur.begin(), cur.end());
+            if (mx - mn <= 3) out.push_back(cur);
+            return;
+        }
+        for (int k = 3; k <= MAX_DIGIT_BITS && k < left; k++) {
+            cur[i] = k;
+            rec(i + 1, left - k);
+        }
+    };
+    if (p == 1) {
+        if (L <= MAX_DIGIT_BITS) out.push_back({L});
+        return;
+    }
+    rec(0, L);
+}
+
+}  // namespace
+}  // namespace zkntt
+
+using namespace zkntt;
+
+extern "C" zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_candidates,
+                                   zkntt_tune_result *best) {
+    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (log_n < 1 || log_n > 28 || max_candidates < 1) return ZKNTT_EINVAL;
+    struct Cand {
+        zkntt_plan_options o;
+    };
+    std::vector<Cand> cands;
+    int pmin = (log_n + MAX_DIGIT_BITS - 1) / MAX_DIGIT_BITS;
+    for (int p = pmin; p <= std::min(4, pmin + 1); p++) {
+        std::vector<std::vector<int>> sp;
+        splits(log_n, p, sp);
+        for (auto &d : sp)
+            for (int mode : {ZKNTT_TWIDDLE_PRECOMP, ZKNTT_TWIDDLE_OTF})
+                for (int cap = 3; cap >= 1; cap--) {
+                    if (p == 1 && (mode == ZKNTT_TWIDDLE_OTF || cap != 3)) continue;
+                    Cand c;
+                    memset(&c.o, 0, sizeof c.o);
+                    c.o.twiddle_mode = mode;
+                    c.o.num_passes = p;
+                    int hi = 0;
+                    for (int i = 0; i < p; i++) {
+                        c.o.digit_bits[i] = d[i];
+                        int span = (i == p - 1) ? hi : (log_n - hi - d[i]);
+                        int lc = std::min({cap, MAX_DIGIT_BITS - d[i], span});
+                        c.o.cols_per_cta[i] = 1 << std::max(0, lc);
+                        hi += d[i];
+                    }
+                    cands.push_back(c);
+                }
+    }
+    // prefer balanced splits and precomputed tables first when the budget is small
+    std::stable_sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) {
+        auto spread = [](const zkntt_plan_options &o) {
+            int mx = 0, mn = 99;
+            for (int i = 0; i < o.num_passes; i++) {
+                mx = std::max(mx, o.digit_bits[i]);
+                mn = std::min(mn, o.digit_bits[i]);
+            }
+            return (mx - mn) * 4 + (o.twiddle_mode == ZKNTT_TWIDDLE_OTF ? 2 : 0);
+        };
+        return spread(a.o) < spread(b.o);
+    });
+    if (int(cands.size()) > max_candidates) cands.resize(max_candidates);
+
+    const size_t bytes = size_t(32) << log_n;
+    void *in = nullptr, *out = nullptr, *scr = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    zkntt_status result = ZKNTT_OK;
+    if (cudaMalloc(&in, bytes) != cudaSuccess || cudaMalloc(&out, bytes) != cudaSuccess ||
+        cudaMalloc(&scr, bytes) != cudaSuccess || cudaStreamCreate(&s) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        result = ZKNTT_ENOMEM;
+    }
+    if (result == ZKNTT_OK) cudaMemset(in, 0, bytes);
+    TuneEntry bestE;
+    double best_ms = 1e30;
+    for (size_t ci = 0; ci < cands.size() && result == ZKNTT_OK; ci++) {
+        zkntt_plan plan = nullptr;
+        if (zkntt_plan_create_ex(&plan, field, log_n, dir, nullptr, &cands[ci].o) != ZKNTT_OK) continue;
+        bool ok = true;
+        for (int w = 0; w < 2 && ok; w++)
+            ok = zkntt_execute_scratch(plan, in, out, scr, bytes, s) == ZKNTT_OK;
+        std::vector<float> t;
+        for (int r = 0; r < 5 && ok; r++) {
+            cudaEventRecord(e0, s);
+            ok = zkntt_execute_scratch(plan, in, out, scr, bytes, s) == ZKNTT_OK;
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t.push_back(ms);
+        }
+        zkntt_plan_destroy(plan);
+        if (!ok || t.empty()) continue;
+        std::sort(t.begin(), t.end());
+        double med = t[t.size() / 2];
+        if (med < best_ms) {
+            best_ms = med;
+            bestE.passes = cands[ci].o.num_passes;
+            for (int i = 0; i < 4; i++) {
+                bestE.digits[i] = cands[ci].o.digit_bits[i];
+                int c = cands[ci].o.cols_per_cta[i], l = 0;
+                while (c > 1) {
+                    c >>= 1;
+                    l++;
+                }
+                bestE.log_cols[i] = i < bestE.passes ? l : -1;
+            }
+            bestE.mode = cands[ci].o.twiddle_mode;
+            bestE.ms = med;
+        }
+    }
+    if (in) cudaFree(in);
+    if (out) cudaFree(out);
+    if (scr) cudaFree(scr);
+    if (s) cudaStreamDestroy(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (result != ZKNTT_OK) return result;
+    if (best_ms >= 1e30) return ZKNTT_ECUDA;
+    tuner_store(field, log_n, dir, bestE);
+    if (best) {
+        best->num_passes = bestE.passes;
+        for (int i = 0; i < 4; i++) {
+            best->digit_bits[i] = bestE.digits[i];
+            best->cols_per_cta[i] = bestE.log_cols[i] >= 0 ? (1 << bestE.log_cols[i]) : 0;
+        }
+        best->twiddle_mode = bestE.mode;
+        best->ms = float(bestE.ms);
+    }
+    return ZKNTT_OK;
+}

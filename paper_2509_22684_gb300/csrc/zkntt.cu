@@ -1,0 +1,1090 @@
+// zkntt.cu -- host runtime and C ABI of the transform library (include/zkntt.h).
+//
+// Host side of the method:
+//  * field constants derived at start-up from the modulus limbs the kernels are
+//    compiled with (R mod r, R^2 mod r, r', roots of unity), using a
+//    separated-operand-scanning Montgomery product on 8 x 32-bit limbs;
+//  * the planner: the digit split of log_n into passes (four-step / six-step,
+//    each digit <= 11 bits so a sub-transform fits one block's shared memory)
+//    and the columns per block;
+//  * resident twiddle tables per plan, generated on the device;
+//  * stream-ordered execution, the persistent batch launch and the Groth16 H
+//    sequence (Fig. 2 of the paper).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/zkntt.h"
+#include "batch.cuh"
+#include "field.cuh"
+#include "kernels.h"
+#include "ntt_pass.cuh"
+#include "tuner.h"
+
+using namespace zkntt;
+
+namespace {
+
+thread_local int g_last_cuda_error = 0;
+
+zkntt_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return ZKNTT_OK;
+    g_last_cuda_error = int(e);
+    cudaGetLastError();  // clear the sticky-free error state of the runtime
+    if (e == cudaErrorMemoryAllocation) return ZKNTT_ENOMEM;
+    return ZKNTT_ECUDA;
+}
+
+#define ZK_CHECK(call)                              \
+    do {                                            \
+        zkntt_status _s = from_cuda(call);          \
+        if (_s != ZKNTT_OK) return _s;              \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// host field arithmetic (Montgomery form, R = 2^256, 8 x 32-bit limbs)
+using E8 = std::array<uint32_t, 8>;
+
+struct HostField {
+    E8 p{};
+    uint32_t rp = 0;   // -p^-1 mod 2^32
+    E8 one{};          // R mod p
+    E8 r2{};           // R^2 mod p
+    uint32_t gen = 0;  // multiplicative generator (plain)
+    int s = 0;         // 2-adicity
+    E8 gen_m{};        // generator, Montgomery form
+    E8 wmax{};         // primitive 2^s-th root, Montgomery form
+    bool ok = false;
+};
+
+bool geq8(const E8 &a, const E8 &b) {
+    for (int i = 7; i >= 0; i--)
+        if (a[i] != b[i]) return a[i] > b[i];
+    return true;
+}
+
+uint32_t add8(E8 &r, const E8 &a, const E8 &b) {
+    uint64_t c = 0;
+    for (int i = 0; i < 8; i++) {
+        c += uint64_t(a[i]) + b[i];
+        r[i] = uint32_t(c);
+        c >>= 32;
+    }
+    return uint32_t(c);
+}
+
+uint32_t sub8(E8 &r, const E8 &a, const E8 &b) {
+    int64_t c = 0;
+    for (int i = 0; i < 8; i++) {
+        c += int64_t(a[i]) - int64_t(b[i]);
+        r[i] = uint32_t(c);
+        c >>= 32;  // arithmetic: 0 or -1
+    }
+    return c ? 1u : 0u;
+}
+
+// SOS: full 512-bit product, then eight word-wise reductions
+E8 hmul(const HostField &F, const E8 &a, const E8 &b) {
+    uint32_t t[17] = {0};
+    for (int i = 0; i < 8; i++) {
+        uint64_t carry = 0;
+        for (int j = 0; j < 8; j++) {
+            uint64_t v = uint64_t(a[i]) * b[j] + t[i + j] + carry;
+            t[i + j] = uint32_t(v);
+            carry = v >> 32;
+        }
+        t[i + 8] = uint32_t(carry);
+    }
+    for (int i = 0; i < 8; i++) {
+        uint32_t m = t[i] * F.rp;
+        uint64_t carry = 0;
+        for (int j = 0; j < 8; j++) {
+            uint64_t v = uint64_t(m) * F.p[j] + t[i + j] + carry;
+            t[i + j] = uint32_t(v);
+            carry = v >> 32;
+        }
+        for (int k = i + 8; carry && k < 17; k++) {
+            uint64_t v = uint64_t(t[k]) + carry;
+            t[k] = uint32_t(v);
+            carry = v >> 32;
+        }
+    }
+    E8 r;
+    for (int i = 0; i < 8; i++) r[i] = t[8 + i];
+    if (t[16] || geq8(r, F.p)) sub8(r, r, F.p);
+    return r;
+}
+
+E8 hsub(const HostField &F, const E8 &a, const E8 &b) {
+    E8 r;
+    if (sub8(r, a, b)) add8(r, r, F.p);
+    return r;
+}
+
+E8 hpow_words(const HostField &F, const E8 &base, const uint32_t *exp_words, int nwords) {
+    E8 acc = F.one, b = base;
+    for (int i = 0; i < 32 * nwords; i++) {
+        if ((exp_words[i / 32] >> (i % 32)) & 1u) acc = hmul(F, acc, b);
+        b = hmul(F, b, b);
+    }
+    return acc;
+}
+
+E8 hpow(const HostField &F, const E8 &base, uint64_t e) {
+    uint32_t w[2] = {uint32_t(e), uint32_t(e >> 32)};
+    return hpow_words(F, base, w, 2);
+}
+
+E8 hinv(const HostField &F, const E8 &a) {
+    E8 e, two{};
+    two[0] = 2;
+    sub8(e, F.p, two);  // Fermat: a^(p-2)
+    return hpow_words(F, a, e.data(), 8);
+}
+
+E8 hto_mont(const HostField &F, uint64_t v) {
+    E8 x{};
+    x[0] = uint32_t(v);
+    x[1] = uint32_t(v >> 32);
+    return hmul(F, x, F.r2);
+}
+
+bool is_zero(const E8 &a) {
+    for (uint32_t v : a)
+        if (v) return false;
+    return true;
+}
+
+template <class FD>
+HostField make_field(uint32_t gen) {
+    HostField F;
+    F.p = {FD::P0, FD::P1, FD::P2, FD::P3, FD::P4, FD::P5, FD::P6, FD::P7};
+    // -p^-1 mod 2^32 by Newton's iteration on the low limb
+    uint32_t inv = 1;
+    for (int i = 0; i < 5; i++) inv *= 2u - F.p[0] * inv;
+    F.rp = 0u - inv;
+    // R mod p: 2^256 - p (two's complement), then subtract p until below p
+    E8 zero{}, x;
+    sub8(x, zero, F.p);
+    while (geq8(x, F.p)) sub8(x, x, F.p);
+    F.one = x;
+    // R^2 mod p: double R mod p 256 times
+    for (int i = 0; i < 256; i++) {
+        E8 y;
+        uint32_t c = add8(y, x, x);
+        if (c || geq8(y, F.p)) sub8(y, y, F.p);
+        x = y;
+    }
+    F.r2 = x;
+    F.gen = gen;
+    E8 pm1, onep{};
+    onep[0] = 1;
+    sub8(pm1, F.p, onep);
+    int s = 0;
+    while (((pm1[s / 32] >> (s % 32)) & 1u) == 0) s++;
+    F.s = s;
+    E8 e{};
+    for (int i = 0; i + s < 256; i++)
+        if ((pm1[(i + s) / 32] >> ((i + s) % 32)) & 1u) e[i / 32] |= 1u << (i % 32);
+    F.gen_m = hto_mont(F, gen);
+    F.wmax = hpow_words(F, F.gen_m, e.data(), 8);
+    // self-check: the root has order exactly 2^s and r' matches the kernels'
+    E8 w = F.wmax;
+    for (int i = 0; i < s - 1; i++) w = hmul(F, w, w);
+    E8 minus_one = hsub(F, E8{}, F.one);
+    F.ok = (w == minus_one) && (F.rp == FD::RP) && (hmul(F, w, w) == F.one);
+    return F;
+}
+
+const HostField &host_field(int id) {
+    static const HostField bls = make_field<FrBLS12_381>(7);
+    static const HostField bn = make_field<FrBN254>(5);
+    return id == 0 ? bls : bn;
+}
+
+const FieldKernels &field_kernels(int id) { return id == 0 ? kernels_bls12_381() : kernels_bn254(); }
+
+uint32_t rev_bits(uint32_t x, int bits) {
+    uint32_t r = 0;
+    for (int i = 0; i < bits; i++) r |= ((x >> i) & 1u) << (bits - 1 - i);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+struct DeviceInfo {
+    int sms = 0;
+    bool init = false;
+    uint32_t *status = nullptr;  // sticky device-side error word
+};
+
+std::mutex g_dev_mu;
+std::map<int, DeviceInfo> g_devices;
+
+zkntt_status device_info(DeviceInfo **out) {
+    int dev = 0;
+    ZK_CHECK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DeviceInfo &d = g_devices[dev];
+    if (!d.init) {
+        ZK_CHECK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+        for (int f = 0; f < 2; f++) {
+            const FieldKernels &k = field_kernels(f);
+            for (int K = 1; K <= MAX_DIGIT_BITS; K++)
+                ZK_CHECK(cudaFuncSetAttribute(k.pass[K], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              64 * 1024));
+        }
+        ZK_CHECK(cudaFuncSetAttribute(batch_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      64 * 1024));
+        ZK_CHECK(cudaMalloc(&d.status, sizeof(uint32_t)));
+        ZK_CHECK(cudaMemset(d.status, 0, sizeof(uint32_t)));
+        // keep freed stream-ordered scratch in the pool between executions
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        d.init = true;
+    }
+    *out = &d;
+    return ZKNTT_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+struct PassPlan {
+    int K = 0, lo_bits = 0, hi_bits = 0, log_cols = 0;
+    int threads = 0, grid = 0;
+    uint32_t num_tiles = 0;
+    size_t smem = 0;
+    uint4 *w_sub = nullptr, *tw = nullptr, *w_hi = nullptr, *w_lo = nullptr, *fl = nullptr,
+          *fd = nullptr;
+    int tw_bits = 0, split_bits = 0;
+};
+
+struct zkntt_plan_s {
+    int field = 0, log_n = 0, dir = 0, coset = 0, mode = 0, passes = 0, device = 0;
+    E8 shift{};
+    PassPlan ps[4];
+    uint4 *pre = nullptr, *post = nullptr;
+    std::vector<void *> allocs;
+    size_t table_bytes = 0;
+    int extra_scalar = 0;  // 1: an extra constant folded into the output scale
+    E8 extra{};
+};
+
+namespace {
+
+zkntt_status dalloc(zkntt_plan_s *P, uint4 **out, size_t elems) {
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, elems * 32);
+    if (e != cudaSuccess) return from_cuda(e);
+    P->allocs.push_back(p);
+    P->table_bytes += elems * 32;
+    *out = static_cast<uint4 *>(p);
+    return ZKNTT_OK;
+}
+
+zkntt_status upload(zkntt_plan_s *P, uint4 **out, const std::vector<E8> &v) {
+    zkntt_status s = dalloc(P, out, v.size());
+    if (s != ZKNTT_OK) return s;
+    return from_cuda(cudaMemcpy(*out, v.data(), v.size() * 32, cudaMemcpyHostToDevice));
+}
+
+void free_plan(zkntt_plan_s *P) {
+    for (void *p : P->allocs) cudaFree(p);
+    P->allocs.clear();
+    delete P;
+}
+
+std::vector<E8> powers(const HostField &F, const E8 &base, size_t count, const E8 &scale) {
+    std::vector<E8> v(count);
+    E8 cur = scale;
+    for (size_t i = 0; i < count; i++) {
+        v[i] = cur;
+        cur = hmul(F, cur, base);
+    }
+    return v;
+}
+
+int grid_for(size_t work, int per_block, int sms) {
+    size_t g = (work + per_block - 1) / per_block;
+    size_t cap = size_t(sms) * 8;
+    return int(std::max<size_t>(1, std::min(g, cap)));
+}
+
+// default digit split and columns (the tuner may override both)
+void default_digits(int L, int *passes, int k[4]) {
+    if (L <= MAX_DIGIT_BITS) {
+        *passes = 1;
+        k[0] = L;
+    } else if (L <= 2 * MAX_DIGIT_BITS) {
+        *passes = 2;
+        k[0] = (L + 1) / 2;
+        k[1] = L - k[0];
+    } else {
+        *passes = 3;
+        k[0] = (L + 2) / 3;
+        k[1] = (L - k[0] + 1) / 2;
+        k[2] = L - k[0] - k[1];
+    }
+}
+
+int default_log_cols(int K, int span_bits) {
+    // tile of C x 2^K elements, at most 2^11 elements (64 KiB); C <= 8 and
+    // C <= the number of columns the pass has (2^span_bits)
+    int lc = std::min(3, MAX_DIGIT_BITS - K);
+    return std::max(0, std::min(lc, span_bits));
+}
+
+zkntt_status launch_gen_twiddle(int field, uint4 *out, int K, int lo_bits, const uint4 *w_hi,
+                                const uint4 *w_lo, int split, const uint4 *fl, const uint4 *fd,
+                                int sms) {
+    const FieldKernels &kk = field_kernels(field);
+    uint32_t uK = K, ulo = lo_bits, usp = split;
+    void *args[] = {&out, &uK, &ulo, &w_hi, &w_lo, &usp, &fl, &fd};
+    size_t total = size_t(1) << (K + lo_bits);
+    return from_cuda(cudaLaunchKernel(kk.gen_twiddle, dim3(grid_for(total, 256, sms)), dim3(256),
+                                      args, 0, nullptr));
+}
+
+zkntt_status launch_gen_powers(int field, uint4 *out, uint32_t count, const uint4 *hi,
+                               const uint4 *lo, int split, int sms) {
+    const FieldKernels &kk = field_kernels(field);
+    uint32_t usp = split;
+    void *args[] = {&out, &count, &hi, &lo, &usp};
+    return from_cuda(cudaLaunchKernel(kk.gen_powers, dim3(grid_for(count, 256, sms)), dim3(256),
+                                      args, 0, nullptr));
+}
+
+// split tables for base^e, e < 2^bits: lo[x] = base^x * scale, hi[y] = base^(y 2^split)
+zkntt_status split_tables(zkntt_plan_s *P, const HostField &F, const E8 &base, int bits,
+                          const E8 &scale, uint4 **hi, uint4 **lo, int *split) {
+    int sp = (bits + 1) / 2;
+    *split = sp;
+    zkntt_status s = upload(P, lo, powers(F, base, size_t(1) << sp, scale));
+    if (s != ZKNTT_OK) return s;
+    E8 step = hpow(F, base, uint64_t(1) << sp);
+    return upload(P, hi, powers(F, step, size_t(1) << (bits - sp), F.one));
+}
+
+zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
+    const HostField &F = host_field(P->field);
+    if (!F.ok) return ZKNTT_ECUDA;
+    DeviceInfo *dev;
+    zkntt_status st = device_info(&dev);
+    if (st != ZKNTT_OK) return st;
+    ZK_CHECK(cudaGetDevice(&P->device));
+    const int L = P->log_n;
+    const bool inverse = P->dir == ZKNTT_INVERSE;
+    const bool coset = P->coset != 0;
+
+    // ---- schedule
+    int k[4] = {0, 0, 0, 0}, cols[4] = {-1, -1, -1, -1};
+    int mode = ZKNTT_TWIDDLE_AUTO;
+    default_digits(L, &P->passes, k);
+    if (opts && opts->use_tuner) {
+        TuneEntry te;
+        if (tuner_lookup(P->field, L, P->dir, &te)) {
+            P->passes = te.passes;
+            for (int i = 0; i < 4; i++) {
+                k[i] = te.digits[i];
+                cols[i] = te.log_cols[i];
+            }
+            mode = te.mode;
+        }
+    }
+    if (opts && opts->num_passes > 0) {
+        if (opts->num_passes > 4) return ZKNTT_EINVAL;
+        int sum = 0;
+        for (int i = 0; i < opts->num_passes; i++) {
+            if (opts->digit_bits[i] < 1 || opts->digit_bits[i] > MAX_DIGIT_BITS) return ZKNTT_EINVAL;
+            sum += opts->digit_bits[i];
+        }
+        if (sum != L) return ZKNTT_EINVAL;
+        P->passes = opts->num_passes;
+        for (int i = 0; i < 4; i++) {
+            k[i] = i < P->passes ? opts->digit_bits[i] : 0;
+            cols[i] = -1;
+        }
+    }
+    if (opts && opts->twiddle_mode) mode = opts->twiddle_mode;
+    if (mode != ZKNTT_TWIDDLE_OTF) mode = ZKNTT_TWIDDLE_PRECOMP;
+    P->mode = mode;
+    const int p = P->passes;
+
+    // ---- scalars
+    E8 w = hpow(F, F.wmax, uint64_t(1) << (F.s - L));  // w_n
+    if (inverse) w = hinv(F, w);
+    const E8 ninv = hinv(F, hto_mont(F, uint64_t(1) << L));
+    const E8 g = P->shift;
+    const E8 ginv = coset ? hinv(F, g) : F.one;
+    E8 out_scale = inverse ? ninv : F.one;  // folded into pass 0 (p > 1) or post (p == 1)
+    if (P->extra_scalar) out_scale = hmul(F, out_scale, P->extra);
+
+    int hi_bits = 0;
+    for (int i = 0; i < p; i++) {
+        PassPlan &ps = P->ps[i];
+        ps.K = k[i];
+        ps.hi_bits = hi_bits;
+        ps.lo_bits = L - hi_bits - k[i];
+        hi_bits += k[i];
+        const bool last = (i == p - 1);
+        const int span = last ? ps.hi_bits : ps.lo_bits;
+        int lc = default_log_cols(ps.K, span);
+        if (opts && opts->cols_per_cta[i] > 0) {
+            int c = opts->cols_per_cta[i], l = 0;
+            while ((1 << l) < c) l++;
+            if ((1 << l) != c || l > 3 || l > span || (ps.K + l) > MAX_DIGIT_BITS) return ZKNTT_EINVAL;
+            lc = l;
+        } else if (cols[i] >= 0 && cols[i] <= std::min(3, span) && ps.K + cols[i] <= MAX_DIGIT_BITS) {
+            lc = cols[i];
+        }
+        ps.log_cols = lc;
+        ps.num_tiles = last ? (uint32_t(1) << (ps.hi_bits - lc))
+                            : (uint32_t(1) << (ps.hi_bits + ps.lo_bits - lc));
+        const int T = ps.K >= 3 ? (1 << (ps.K - 3)) : 1;
+        ps.threads = T << lc;
+        ps.smem = size_t(32) << (ps.K + lc);
+        int nb = 0;
+        ZK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, field_kernels(P->field).pass[ps.K], ps.threads, ps.smem));
+        nb = std::max(nb, 1);
+        ps.grid = int(std::min<uint64_t>(ps.num_tiles, uint64_t(nb) * dev->sms));
+
+        // sub-transform twiddles w_N^e, e < N/2
+        const E8 wn_i = hpow(F, w, uint64_t(1) << ps.hi_bits);          // root of order n_i
+        const E8 wN = hpow(F, wn_i, uint64_t(1) << ps.lo_bits);         // root of order N_i
+        st = upload(P, &ps.w_sub, powers(F, wN, std::max<size_t>(1, (size_t(1) << ps.K) / 2), F.one));
+        if (st != ZKNTT_OK) return st;
+
+        // per-row coset-inverse factor for this digit: g^-(rev(d) * 2^hi_bits)
+        std::vector<E8> phi;
+        if (coset && inverse) {
+            const E8 gstep = hpow(F, ginv, uint64_t(1) << ps.hi_bits);
+            std::vector<E8> pw = powers(F, gstep, size_t(1) << ps.K, F.one);
+            phi.resize(pw.size());
+            for (uint32_t d = 0; d < pw.size(); d++) phi[d] = pw[rev_bits(d, ps.K)];
+        }
+        if (!last) {
+            ps.tw_bits = ps.K + ps.lo_bits;
+            const E8 scale = (i == 0) ? out_scale : F.one;
+            st = split_tables(P, F, wn_i, ps.tw_bits, scale, &ps.w_hi, &ps.w_lo, &ps.split_bits);
+            if (st != ZKNTT_OK) return st;
+            if (i == 0 && coset && !inverse) {
+                // column factor g^lo, lo < 2^lo_bits
+                uint4 *ghi, *glo;
+                int gsp;
+                st = split_tables(P, F, g, ps.lo_bits, F.one, &ghi, &glo, &gsp);
+                if (st != ZKNTT_OK) return st;
+                st = dalloc(P, &ps.fl, size_t(1) << ps.lo_bits);
+                if (st != ZKNTT_OK) return st;
+                st = launch_gen_powers(P->field, ps.fl, uint32_t(1) << ps.lo_bits, ghi, glo, gsp, dev->sms);
+                if (st != ZKNTT_OK) return st;
+            }
+            if (!phi.empty()) {
+                st = upload(P, &ps.fd, phi);
+                if (st != ZKNTT_OK) return st;
+            }
+            if (mode == ZKNTT_TWIDDLE_PRECOMP) {
+                st = dalloc(P, &ps.tw, size_t(1) << (ps.K + ps.lo_bits));
+                if (st != ZKNTT_OK) return st;
+                st = launch_gen_twiddle(P->field, ps.tw, ps.K, ps.lo_bits, ps.w_hi, ps.w_lo,
+                                        ps.split_bits, ps.fl, ps.fd, dev->sms);
+                if (st != ZKNTT_OK) return st;
+            }
+        } else {
+            // output scale on the last pass: coset-inverse row factor, and for a
+            // single pass also n^-1 and any extra constant
+            const bool need_scalar = (p == 1) && !(out_scale == F.one);
+            if (!phi.empty() || need_scalar) {
+                const size_t N = size_t(1) << ps.K;
+                std::vector<E8> q(N, p == 1 ? out_scale : F.one);
+                if (!phi.empty())
+                    for (size_t d = 0; d < N; d++) q[d] = hmul(F, q[d], phi[d]);
+                st = upload(P, &P->post, q);
+                if (st != ZKNTT_OK) return st;
+            }
+        }
+        if (i == 0 && coset && !inverse) {
+            // input row factor (g^(2^lo_bits))^d
+            const E8 gs = hpow(F, g, uint64_t(1) << ps.lo_bits);
+            st = upload(P, &P->pre, powers(F, gs, size_t(1) << ps.K, F.one));
+            if (st != ZKNTT_OK) return st;
+        }
+    }
+    // tables are generated on the legacy stream; make them visible to all streams
+    return from_cuda(cudaDeviceSynchronize());
+}
+
+PassArgs pass_args(const zkntt_plan_s *P, int i, const void *in, void *out) {
+    const PassPlan &ps = P->ps[i];
+    PassArgs a;
+    memset(&a, 0, sizeof a);
+    a.in = static_cast<const uint4 *>(in);
+    a.out = static_cast<uint4 *>(out);
+    a.w_sub = ps.w_sub;
+    a.tw = ps.tw;
+    a.w_hi = ps.w_hi;
+    a.w_lo = ps.w_lo;
+    a.fl = ps.fl;
+    a.fd = ps.fd;
+    a.pre = (i == 0) ? P->pre : nullptr;
+    a.post = (i == P->passes - 1) ? P->post : nullptr;
+    a.pw_b = nullptr;
+    a.pw_c = nullptr;
+    a.lo_bits = ps.lo_bits;
+    a.hi_bits = ps.hi_bits;
+    a.tw_bits = ps.tw_bits;
+    a.split_bits = ps.split_bits;
+    a.log_cols = ps.log_cols;
+    a.last = (i == P->passes - 1);
+    a.otf = (P->mode == ZKNTT_TWIDDLE_OTF);
+    a.num_tiles = ps.num_tiles;
+    return a;
+}
+
+bool bad_ptr(const void *p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 31u); }
+
+bool partial_overlap(const void *a, const void *b, size_t bytes) {
+    uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    if (x == y) return false;
+    return x < y + bytes && y < x + bytes;
+}
+
+// [a, a + na) and [b, b + nb) share at least one byte
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb) {
+    uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
+zkntt_status run_passes(const zkntt_plan_s *P, const void *in, void *out, void *scratch,
+                        cudaStream_t s) {
+    const FieldKernels &kk = field_kernels(P->field);
+    for (int i = 0; i < P->passes; i++) {
+        const void *src = (i == 0) ? in : scratch;
+        void *dst = (i == P->passes - 1) ? out : scratch;
+        PassArgs a = pass_args(P, i, src, dst);
+        void *args[] = {&a};
+        const PassPlan &ps = P->ps[i];
+        ZK_CHECK(cudaLaunchKernel(kk.pass[ps.K], dim3(ps.grid), dim3(ps.threads), args, ps.smem, s));
+    }
+    return ZKNTT_OK;
+}
+
+size_t scratch_bytes_of(const zkntt_plan_s *P) {
+    return P->passes > 1 ? (size_t(32) << P->log_n) : 0;
+}
+
+zkntt_status create_plan(zkntt_plan *out, zkntt_field field, int log_n, zkntt_dir dir,
+                         const uint32_t *coset_shift, const zkntt_plan_options *opts,
+                         const E8 *extra) {
+    if (!out) return ZKNTT_EINVAL;
+    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (dir != ZKNTT_FORWARD && dir != ZKNTT_INVERSE) return ZKNTT_EINVAL;
+    const HostField &F = host_field(field);
+    if (log_n < 1 || log_n > std::min(F.s, 28)) return ZKNTT_EINVAL;
+    if (opts && (opts->twiddle_mode < 0 || opts->twiddle_mode > 2)) return ZKNTT_EINVAL;
+    zkntt_plan_s *P = new (std::nothrow) zkntt_plan_s;
+    if (!P) return ZKNTT_ENOMEM;
+    P->field = field;
+    P->log_n = log_n;
+    P->dir = dir;
+    if (coset_shift) {
+        for (int i = 0; i < 8; i++) P->shift[i] = coset_shift[i];
+        if (is_zero(P->shift) || geq8(P->shift, F.p)) {
+            delete P;
+            return ZKNTT_EINVAL;
+        }
+        P->coset = 1;
+    }
+    if (extra) {
+        P->extra_scalar = 1;
+        P->extra = *extra;
+    }
+    zkntt_status s = build_plan(P, opts);
+    if (s != ZKNTT_OK) {
+        free_plan(P);
+        return s;
+    }
+    *out = P;
+    return ZKNTT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batch construction
+struct JobSpec {
+    const zkntt_plan_s *plan;
+    const void *in;
+    void *out;
+    void *scratch;
+    const void *pw_b = nullptr, *pw_c = nullptr;  // fused pointwise on the first pass
+    int level0 = 0;                               // level of the job's first pass
+    int deps[3] = {-1, -1, -1};                   // jobs whose last pass must finish first
+};
+
+zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
+                          unsigned long long timeout_ns) {
+    DeviceInfo *dev;
+    zkntt_status st = device_info(&dev);
+    if (st != ZKNTT_OK) return st;
+    struct SegTmp {
+        int job, pass, level;
+    };
+    std::vector<SegTmp> segs;
+    for (int j = 0; j < int(jobs.size()); j++)
+        for (int i = 0; i < jobs[j].plan->passes; i++) segs.push_back({j, i, jobs[j].level0 + i});
+    std::stable_sort(segs.begin(), segs.end(),
+                     [](const SegTmp &a, const SegTmp &b) { return a.level < b.level; });
+    if (segs.size() > size_t(BATCH_MAX_SEGMENTS)) return ZKNTT_EUNSUPPORTED;
+    std::map<std::pair<int, int>, int> index;
+    for (int k = 0; k < int(segs.size()); k++) index[{segs[k].job, segs[k].pass}] = k;
+
+    BatchTable *tab = new (std::nothrow) BatchTable;
+    if (!tab) return ZKNTT_ENOMEM;
+    memset(tab, 0, sizeof *tab);
+    tab->nseg = uint32_t(segs.size());
+    tab->timeout_ns = timeout_ns;
+    uint32_t item = 0;
+    for (int k = 0; k < int(segs.size()); k++) {
+        const JobSpec &J = jobs[segs[k].job];
+        const zkntt_plan_s *P = J.plan;
+        const int i = segs[k].pass;
+        const void *src = (i == 0) ? J.in : J.scratch;
+        void *dst = (i == P->passes - 1) ? J.out : J.scratch;
+        BatchSeg &sg = tab->seg[k];
+        sg.a = pass_args(P, i, src, dst);
+        if (i == 0) {
+            sg.a.pw_b = static_cast<const uint4 *>(J.pw_b);
+            sg.a.pw_c = static_cast<const uint4 *>(J.pw_c);
+        }
+        sg.field = uint32_t(P->field);
+        sg.K = uint32_t(P->ps[i].K);
+        sg.first_item = item;
+        item += P->ps[i].num_tiles;
+        for (int d = 0; d < 3; d++) {
+            sg.dep[d] = -1;
+            sg.dep_tiles[d] = 0;
+        }
+        if (i > 0) {
+            int dk = index[{segs[k].job, i - 1}];
+            sg.dep[0] = dk;
+            sg.dep_tiles[0] = jobs[segs[k].job].plan->ps[i - 1].num_tiles;
+        } else {
+            for (int d = 0; d < 3; d++) {
+                int dj = J.deps[d];
+                if (dj < 0) continue;
+                const zkntt_plan_s *DP = jobs[dj].plan;
+                int dk = index[{dj, DP->passes - 1}];
+                sg.dep[d] = dk;
+                sg.dep_tiles[d] = DP->ps[DP->passes - 1].num_tiles;
+            }
+        }
+    }
+    tab->total_items = item;
+
+    uint32_t *ctrl = nullptr;
+    const size_t words = 2 + segs.size();
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&ctrl), words * 4, s);
+    if (e != cudaSuccess) {
+        delete tab;
+        return from_cuda(e);
+    }
+    e = cudaMemsetAsync(ctrl, 0, words * 4, s);
+    if (e == cudaSuccess) {
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel_ptr(), BATCH_THREADS,
+                                                          64 * 1024);
+        nb = std::max(nb, 1);
+        uint32_t grid = std::min<uint32_t>(item, uint32_t(nb) * dev->sms);
+        uint32_t *done = ctrl + 2;
+        uint32_t *status = dev->status;
+        void *args[] = {tab, &ctrl, &done, &status};
+        if (e == cudaSuccess && grid > 0)
+            e = cudaLaunchKernel(batch_kernel_ptr(), dim3(grid), dim3(BATCH_THREADS), args,
+                                 64 * 1024, s);
+    }
+    cudaError_t e2 = cudaFreeAsync(ctrl, s);
+    delete tab;
+    if (e != cudaSuccess) return from_cuda(e);
+    return from_cuda(e2);
+}
+
+unsigned long long batch_timeout_ns() {
+    const char *v = getenv("ZKNTT_BATCH_TIMEOUT_MS");
+    unsigned long long ms = v ? strtoull(v, nullptr, 10) : 2000ull;
+    if (ms == 0) ms = 2000;
+    return ms * 1000000ull;
+}
+
+// Groth16 plans per (field, log_n): iNTT, coset NTT, coset iNTT, and the coset
+// iNTT with (g^n - 1)^-1 folded into its output scale (fused form)
+struct G16Plans {
+    zkntt_plan intt = nullptr, cntt = nullptr, cintt = nullptr, cintt_z = nullptr;
+    E8 zinv{};
+};
+std::mutex g_g16_mu;
+std::map<std::pair<int, std::pair<int, int>>, G16Plans> g_g16;
+
+zkntt_status g16_plans(int field, int log_n, G16Plans **out) {
+    int dev = 0;
+    ZK_CHECK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_g16_mu);
+    G16Plans &G = g_g16[{dev, {field, log_n}}];
+    if (!G.intt) {
+        const HostField &F = host_field(field);
+        const E8 g = F.gen_m;
+        E8 gn = hpow(F, g, uint64_t(1) << log_n);
+        G.zinv = hinv(F, hsub(F, gn, F.one));
+        zkntt_status s;
+        zkntt_plan_options o;
+        memset(&o, 0, sizeof o);
+        o.use_tuner = 1;
+        if ((s = create_plan(&G.intt, zkntt_field(field), log_n, ZKNTT_INVERSE, nullptr, &o, nullptr)) ||
+            (s = create_plan(&G.cntt, zkntt_field(field), log_n, ZKNTT_FORWARD, g.data(), &o, nullptr)) ||
+            (s = create_plan(&G.cintt, zkntt_field(field), log_n, ZKNTT_INVERSE, g.data(), &o, nullptr)) ||
+            (s = create_plan(&G.cintt_z, zkntt_field(field), log_n, ZKNTT_INVERSE, g.data(), &o, &G.zinv))) {
+            for (zkntt_plan *q : {&G.intt, &G.cntt, &G.cintt, &G.cintt_z})
+                if (*q) {
+                    free_plan(*q);
+                    *q = nullptr;
+                }
+            return s;
+        }
+    }
+    *out = &G;
+    return ZKNTT_OK;
+}
+
+zkntt_status launch_pointwise(int field, const void *a, const void *b, const void *c,
+                              const void *z_dev, void *h, size_t n, cudaStream_t s) {
+    DeviceInfo *dev;
+    zkntt_status st = device_info(&dev);
+    if (st != ZKNTT_OK) return st;
+    void *args[] = {&a, &b, &c, &z_dev, &h, &n};
+    return from_cuda(cudaLaunchKernel(field_kernels(field).pointwise,
+                                      dim3(grid_for(n, 256, dev->sms)), dim3(256), args, 0, s));
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+extern "C" {
+
+zkntt_status zkntt_plan_create(zkntt_plan *out, zkntt_field field, int log_n, zkntt_dir dir,
+                               const uint32_t *coset_shift) {
+    return create_plan(out, field, log_n, dir, coset_shift, nullptr, nullptr);
+}
+
+zkntt_status zkntt_plan_create_ex(zkntt_plan *out, zkntt_field field, int log_n, zkntt_dir dir,
+                                  const uint32_t *coset_shift, const zkntt_plan_options *opts) {
+    return create_plan(out, field, log_n, dir, coset_shift, opts, nullptr);
+}
+
+zkntt_status zkntt_plan_destroy(zkntt_plan plan) {
+    if (plan) free_plan(plan);
+    return ZKNTT_OK;
+}
+
+zkntt_status zkntt_plan_scratch_bytes(zkntt_plan plan, size_t *bytes) {
+    if (!plan || !bytes) return ZKNTT_EINVAL;
+    *bytes = scratch_bytes_of(plan);
+    return ZKNTT_OK;
+}
+
+zkntt_status zkntt_plan_describe(zkntt_plan plan, int *num_passes, int digit_bits[4],
+                                 int *twiddle_mode, size_t *table_bytes) {
+    if (!plan) return ZKNTT_EINVAL;
+    if (num_passes) *num_passes = plan->passes;
+    if (digit_bits)
+        for (int i = 0; i < 4; i++) digit_bits[i] = i < plan->passes ? plan->ps[i].K : 0;
+    if (twiddle_mode) *twiddle_mode = plan->mode;
+    if (table_bytes) *table_bytes = plan->table_bytes;
+    return ZKNTT_OK;
+}
+
+zkntt_status zkntt_execute_scratch(zkntt_plan plan, const void *d_in, void *d_out, void *d_scratch,
+                                   size_t scratch_bytes, void *stream) {
+    if (!plan || bad_ptr(d_in) || bad_ptr(d_out)) return ZKNTT_EINVAL;
+    const size_t bytes = size_t(32) << plan->log_n;
+    if (partial_overlap(d_in, d_out, bytes)) return ZKNTT_EINVAL;
+    const size_t need = scratch_bytes_of(plan);
+    if (need) {
+        if (bad_ptr(d_scratch) || scratch_bytes < need) return ZKNTT_EINVAL;
+        if (ranges_overlap(d_scratch, need, d_in, bytes) || ranges_overlap(d_scratch, need, d_out, bytes))
+            return ZKNTT_EINVAL;
+    }
+    return run_passes(plan, d_in, d_out, d_scratch, static_cast<cudaStream_t>(stream));
+}
+
+zkntt_status zkntt_execute(zkntt_plan plan, const void *d_in, void *d_out, void *stream) {
+    if (!plan || bad_ptr(d_in) || bad_ptr(d_out)) return ZKNTT_EINVAL;
+    const size_t bytes = size_t(32) << plan->log_n;
+    if (partial_overlap(d_in, d_out, bytes)) return ZKNTT_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t need = scratch_bytes_of(plan);
+    void *scratch = nullptr;
+    if (need) ZK_CHECK(cudaMallocAsync(&scratch, need, s));
+    zkntt_status st = run_passes(plan, d_in, d_out, scratch, s);
+    if (scratch) {
+        zkntt_status st2 = from_cuda(cudaFreeAsync(scratch, s));
+        if (st == ZKNTT_OK) st = st2;
+    }
+    return st;
+}
+
+zkntt_status zkntt_execute_host(zkntt_plan plan, const void *h_in, void *h_out, void *stream) {
+    if (!plan || !h_in || !h_out) return ZKNTT_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = size_t(32) << plan->log_n;
+    const size_t need = scratch_bytes_of(plan);
+    char *buf = nullptr;
+    ZK_CHECK(cudaMallocAsync(reinterpret_cast<void **>(&buf), bytes + need, s));
+    zkntt_status st = from_cuda(cudaMemcpyAsync(buf, h_in, bytes, cudaMemcpyHostToDevice, s));
+    if (st == ZKNTT_OK) st = run_passes(plan, buf, buf, need ? buf + bytes : nullptr, s);
+    if (st == ZKNTT_OK) st = from_cuda(cudaMemcpyAsync(h_out, buf, bytes, cudaMemcpyDeviceToHost, s));
+    zkntt_status st2 = from_cuda(cudaFreeAsync(buf, s));
+    return st != ZKNTT_OK ? st : st2;
+}
+
+zkntt_status zkntt_execute_batch(const zkntt_plan *plans, const zkntt_io *ptrs, int count,
+                                 void *stream) {
+    if (count < 0 || (count > 0 && (!plans || !ptrs))) return ZKNTT_EINVAL;
+    if (count == 0) return ZKNTT_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    size_t scratch_total = 0;
+    for (int j = 0; j < count; j++) {
+        if (!plans[j] || bad_ptr(ptrs[j].d_in) || bad_ptr(ptrs[j].d_out)) return ZKNTT_EINVAL;
+        const size_t bytes = size_t(32) << plans[j]->log_n;
+        if (partial_overlap(ptrs[j].d_in, ptrs[j].d_out, bytes)) return ZKNTT_EINVAL;
+        scratch_total += scratch_bytes_of(plans[j]);
+    }
+    char *scratch = nullptr;
+    if (scratch_total) ZK_CHECK(cudaMallocAsync(reinterpret_cast<void **>(&scratch), scratch_total, s));
+    std::vector<JobSpec> jobs(count);
+    size_t off = 0;
+    for (int j = 0; j < count; j++) {
+        jobs[j].plan = plans[j];
+        jobs[j].in = ptrs[j].d_in;
+        jobs[j].out = ptrs[j].d_out;
+        jobs[j].scratch = scratch_bytes_of(plans[j]) ? scratch + off : nullptr;
+        off += scratch_bytes_of(plans[j]);
+    }
+    // chunk so that each launch stays within the segment table
+    zkntt_status st = ZKNTT_OK;
+    size_t b = 0;
+    while (b < jobs.size() && st == ZKNTT_OK) {
+        size_t e = b, segs = 0;
+        while (e < jobs.size() && segs + jobs[e].plan->passes <= size_t(BATCH_MAX_SEGMENTS)) {
+            segs += jobs[e].plan->passes;
+            e++;
+        }
+        std::vector<JobSpec> chunk(jobs.begin() + b, jobs.begin() + e);
+        st = launch_batch(chunk, s, batch_timeout_ns());
+        b = e;
+    }
+    if (scratch) {
+        zkntt_status st2 = from_cuda(cudaFreeAsync(scratch, s));
+        if (st == ZKNTT_OK) st = st2;
+    }
+    return st;
+}
+
+zkntt_status zkntt_groth16_h(zkntt_field field, int log_n, const void *d_a, const void *d_b,
+                             const void *d_c, void *d_h, void *d_scratch, int fused, void *stream) {
+    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (log_n < 1 || log_n > 28) return ZKNTT_EINVAL;
+    if (bad_ptr(d_a) || bad_ptr(d_b) || bad_ptr(d_c) || bad_ptr(d_h) || bad_ptr(d_scratch))
+        return ZKNTT_EINVAL;
+    const size_t bytes = size_t(32) << log_n;
+    char *S = static_cast<char *>(d_scratch);
+    for (const void *q : {d_a, d_b, d_c, (const void *)d_h})
+        if (ranges_overlap(q, bytes, S, 3 * bytes)) return ZKNTT_EINVAL;
+    for (const void *q : {d_a, d_b, d_c})
+        if (ranges_overlap(q, bytes, d_h, bytes)) return ZKNTT_EINVAL;
+    G16Plans *G;
+    zkntt_status st = g16_plans(field, log_n, &G);
+    if (st != ZKNTT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *S0 = S, *S1 = S + bytes, *S2 = S + 2 * bytes;
+    const void *in[3] = {d_a, d_b, d_c};
+    void *sv[3] = {S0, S1, S2};
+    if (!fused) {
+        for (int k = 0; k < 3; k++)
+            if ((st = zkntt_execute(G->intt, in[k], sv[k], s))) return st;
+        for (int k = 0; k < 3; k++)
+            if ((st = zkntt_execute(G->cntt, sv[k], sv[k], s))) return st;
+        uint4 *z = nullptr;
+        ZK_CHECK(cudaMallocAsync(reinterpret_cast<void **>(&z), 32, s));
+        st = from_cuda(cudaMemcpyAsync(z, G->zinv.data(), 32, cudaMemcpyHostToDevice, s));
+        if (st == ZKNTT_OK) st = launch_pointwise(field, S0, S1, S2, z, d_h, size_t(1) << log_n, s);
+        zkntt_status st2 = from_cuda(cudaFreeAsync(z, s));
+        if (st != ZKNTT_OK) return st;
+        if (st2 != ZKNTT_OK) return st2;
+        return zkntt_execute(G->cintt, d_h, d_h, s);
+    }
+    // fused: one persistent launch over the dependency graph
+    //   jobs 0-2: iNTT(a|b|c) -> S0|S1|S2           levels 0 .. p-1
+    //   jobs 3-5: cosetNTT in place on S0|S1|S2      levels p .. 2p-1
+    //   job 6:    cosetINTT((S0*S1 - S2)) * zinv -> h levels 2p .. 3p-1
+    const size_t per = scratch_bytes_of(G->intt);
+    char *ps = nullptr;
+    if (per) ZK_CHECK(cudaMallocAsync(reinterpret_cast<void **>(&ps), 7 * per, s));
+    std::vector<JobSpec> jobs(7);
+    const int p = G->intt->passes;
+    for (int k = 0; k < 3; k++) {
+        jobs[k].plan = G->intt;
+        jobs[k].in = in[k];
+        jobs[k].out = sv[k];
+        jobs[k].level0 = 0;
+        jobs[3 + k].plan = G->cntt;
+        jobs[3 + k].in = sv[k];
+        jobs[3 + k].out = sv[k];
+        jobs[3 + k].level0 = p;
+        jobs[3 + k].deps[0] = k;
+    }
+    jobs[6].plan = G->cintt_z;
+    jobs[6].in = S0;
+    jobs[6].out = d_h;
+    jobs[6].pw_b = S1;
+    jobs[6].pw_c = S2;
+    jobs[6].level0 = 2 * p;
+    jobs[6].deps[0] = 3;
+    jobs[6].deps[1] = 4;
+    jobs[6].deps[2] = 5;
+    for (int j = 0; j < 7; j++) jobs[j].scratch = per ? ps + j * per : nullptr;
+    st = launch_batch(jobs, s, batch_timeout_ns());
+    if (ps) {
+        zkntt_status st2 = from_cuda(cudaFreeAsync(ps, s));
+        if (st == ZKNTT_OK) st = st2;
+    }
+    return st;
+}
+
+const char *zkntt_status_str(zkntt_status status) {
+    switch (status) {
+        case ZKNTT_OK: return "ok";
+        case ZKNTT_EINVAL: return "invalid argument";
+        case ZKNTT_ENOMEM: return "out of device memory";
+        case ZKNTT_ECUDA: return "CUDA error";
+        case ZKNTT_ETIMEOUT: return "device-side wait timed out";
+        case ZKNTT_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+zkntt_status zkntt_last_cuda_error(int *err) {
+    if (!err) return ZKNTT_EINVAL;
+    *err = g_last_cuda_error;
+    return ZKNTT_OK;
+}
+
+zkntt_status zkntt_sync_status(void *stream) {
+    ZK_CHECK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    DeviceInfo *dev;
+    zkntt_status st = device_info(&dev);
+    if (st != ZKNTT_OK) return st;
+    uint32_t word = 0;
+    ZK_CHECK(cudaMemcpy(&word, dev->status, 4, cudaMemcpyDeviceToHost));
+    if (word) {
+        ZK_CHECK(cudaMemset(dev->status, 0, 4));
+        if (word & BATCH_STATUS_TIMEOUT) return ZKNTT_ETIMEOUT;
+        return ZKNTT_ECUDA;
+    }
+    return ZKNTT_OK;
+}
+
+zkntt_status zkntt_selftest_timeout(int timeout_ms, void *stream) {
+    if (timeout_ms < 1 || timeout_ms > 10000) return ZKNTT_EINVAL;
+    DeviceInfo *dev;
+    zkntt_status st = device_info(&dev);
+    if (st != ZKNTT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    BatchTable *tab = new (std::nothrow) BatchTable;
+    if (!tab) return ZKNTT_ENOMEM;
+    memset(tab, 0, sizeof *tab);
+    // one segment with one tile that waits for its own completion: the wait can
+    // only end by the time limit, and the tile body never runs
+    tab->nseg = 1;
+    tab->total_items = 1;
+    tab->timeout_ns = (unsigned long long)timeout_ms * 1000000ull;
+    tab->seg[0].K = 4;
+    tab->seg[0].first_item = 0;
+    tab->seg[0].dep[0] = 0;
+    tab->seg[0].dep[1] = tab->seg[0].dep[2] = -1;
+    tab->seg[0].dep_tiles[0] = 1;
+    uint32_t *ctrl = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&ctrl), 3 * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctrl, 0, 3 * 4, s);
+    if (e == cudaSuccess) {
+        uint32_t *done = ctrl + 2;
+        uint32_t *status = dev->status;
+        void *args[] = {tab, &ctrl, &done, &status};
+        e = cudaLaunchKernel(batch_kernel_ptr(), dim3(1), dim3(BATCH_THREADS), args, 64 * 1024, s);
+    }
+    if (ctrl) cudaFreeAsync(ctrl, s);
+    delete tab;
+    if (e != cudaSuccess) return from_cuda(e);
+    return zkntt_sync_status(stream);
+}
+
+zkntt_status zkntt_field_info(zkntt_field field, uint32_t modulus[8], uint32_t generator_mont[8],
+                              int *two_adicity) {
+    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    const HostField &F = host_field(field);
+    if (!F.ok) return ZKNTT_ECUDA;
+    if (modulus) memcpy(modulus, F.p.data(), 32);
+    if (generator_mont) memcpy(generator_mont, F.gen_m.data(), 32);
+    if (two_adicity) *two_adicity = F.s;
+    return ZKNTT_OK;
+}
+
+zkntt_status zkntt_field_op(zkntt_field field, int op, const void *d_a, const void *d_b, void *d_c,
+                            size_t n, void *stream) {
+    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (op < 0 || op > 2) return ZKNTT_EINVAL;
+    if (n == 0) return ZKNTT_OK;
+    if (bad_ptr(d_a) || bad_ptr(d_b) || bad_ptr(d_c)) return ZKNTT_EINVAL;
+    DeviceInfo *dev;
+    zkntt_status st = device_info(&dev);
+    if (st != ZKNTT_OK) return st;
+    void *args[] = {&op, &d_a, &d_b, &d_c, &n};
+    return from_cuda(cudaLaunchKernel(field_kernels(field).field_op, dim3(grid_for(n, 256, dev->sms)),
+                                      dim3(256), args, 0, static_cast<cudaStream_t>(stream)));
+}
+
+zkntt_status zkntt_pointwise(zkntt_field field, const void *d_a, const void *d_b, const void *d_c,
+                             const uint32_t *z_mont, void *d_h, size_t n, void *stream) {
+    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (!z_mont) return ZKNTT_EINVAL;
+    if (n == 0) return ZKNTT_OK;
+    if (bad_ptr(d_a) || bad_ptr(d_b) || bad_ptr(d_c) || bad_ptr(d_h)) return ZKNTT_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *z = nullptr;
+    ZK_CHECK(cudaMallocAsync(&z, 32, s));
+    zkntt_status st = from_cuda(cudaMemcpyAsync(z, z_mont, 32, cudaMemcpyHostToDevice, s));
+    if (st == ZKNTT_OK) st = launch_pointwise(field, d_a, d_b, d_c, z, d_h, n, s);
+    zkntt_status st2 = from_cuda(cudaFreeAsync(z, s));
+    return st != ZKNTT_OK ? st : st2;
+}
+
+zkntt_status zkntt_mulbench(zkntt_field field, int blocks, int threads, int iters, void *d_sink,
+                            void *stream) {
+    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (blocks < 1 || threads < 32 || threads > 256 || iters < 1 || !d_sink) return ZKNTT_EINVAL;
+    void *args[] = {&iters, &d_sink};
+    return from_cuda(cudaLaunchKernel(field_kernels(field).mulbench, dim3(blocks), dim3(threads),
+                                      args, 0, static_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+"""Persistent batch launch and the Groth16 H sequence: every result equals the
+oracle's and the solo execution's, bit for bit; the bounded device wait
+reports a timeout instead of hanging."""
+import numpy as np
+import pytest
+
+from oracle import cpu
+from oracle import field as fld
+from oracle import ntt_ref as ref
+from workloads import batch_jobs, uniform_elements
+
+from gpu_util import first_mismatch, rand_dev, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+FMAP = {"bls12_381_fr": fld.BLS12_381, "bn254_fr": fld.BN254}
+
+
+def _oracle(F, X, inverse=False, shift=None):
+    if X.shape[0] <= 1 << 10:
+        return ref.ntt_mont(F, X, inverse=inverse, shift_mont=shift)
+    return cpu.ntt(F, X, inverse=inverse, shift_mont=shift)
+
+
+def test_batch_uneven_mixed_fields_matches_oracle_and_solo():
+    import torch
+    import paper_2509_22684_gb300 as zk
+    jobs = batch_jobs(4000, count=64, lmin=10, lmax=20)
+    plans, xs, outs, hosts = [], [], [], []
+    for j in jobs:
+        F = FMAP[j.field]
+        X = uniform_elements(F.r, 1 << j.log_n, j.seed)
+        hosts.append(X)
+        xs.append(to_dev(X))
+        outs.append(torch.empty_like(xs[-1]))
+        plans.append(zk.Plan(j.field, j.log_n, inverse=(j.kind == "intt")))
+    zk.execute_batch(plans, xs, outs)
+    zk.sync_status()
+    for j, p, X, x, o in zip(jobs, plans, hosts, xs, outs):
+        F = FMAP[j.field]
+        got = to_host(o)
+        want = _oracle(F, X, inverse=(j.kind == "intt"))
+        assert np.array_equal(got, want), (j, first_mismatch(got, want))
+        solo = to_host(p.execute(x))
+        assert np.array_equal(solo, got)
+    for p in plans:
+        p.close()
+
+
+def test_batch_in_place_and_order_independence():
+    import torch
+    import paper_2509_22684_gb300 as zk
+    F = fld.BN254
+    sizes = [14, 11, 18, 12]
+    Xs = [uniform_elements(F.r, 1 << L, 90 + L) for L in sizes]
+    plans = [zk.Plan(F.name, L, coset_shift=F.to_mont(F.g)) for L in sizes]
+    wants = [_oracle(F, X, shift=F.to_mont(F.g)) for X in Xs]
+    for order in ([0, 1, 2, 3], [3, 1, 0, 2]):
+        xs = [to_dev(Xs[i]) for i in order]
+        zk.execute_batch([plans[i] for i in order], xs, xs)   # in place
+        for k, i in enumerate(order):
+            assert np.array_equal(to_host(xs[k]), wants[i])
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.parametrize("F", [fld.BLS12_381, fld.BN254], ids=lambda f: f.name)
+@pytest.mark.parametrize("L", [4, 10, 13, 16])
+@pytest.mark.parametrize("fused", [False, True])
+def test_groth16_matches_oracle(F, L, fused):
+    import paper_2509_22684_gb300 as zk
+    A, B, C = (uniform_elements(F.r, 1 << L, s) for s in (3001, 3002, 3003))
+    a, b, c = (to_dev(v) for v in (A, B, C))
+    h = zk.groth16_h(F.name, L, a, b, c, fused=fused)
+    zk.sync_status()
+    got = to_host(h)
+    want = ref.groth16_h_mont(F, A, B, C) if L <= 10 else cpu.groth16_h(F, A, B, C)
+    assert np.array_equal(got, want), first_mismatch(got, want)
+    # the inputs are read only
+    assert np.array_equal(to_host(a), A)
+
+
+def test_groth16_2_22_fused_equals_separate_and_oracle():
+    import paper_2509_22684_gb300 as zk
+    F = fld.BLS12_381
+    L = 22
+    A, B, C = (uniform_elements(F.r, 1 << L, s) for s in (3001, 3002, 3003))
+    a, b, c = (to_dev(v) for v in (A, B, C))
+    h1 = to_host(zk.groth16_h(F.name, L, a, b, c, fused=True))
+    h0 = to_host(zk.groth16_h(F.name, L, a, b, c, fused=False))
+    assert np.array_equal(h0, h1)
+    want = cpu.groth16_h(F, A, B, C)
+    assert np.array_equal(h1, want), first_mismatch(h1, want)
+
+
+def test_groth16_constrained_top_coefficient_zero():
+    """c = a*b on the domain: h has degree <= n-2 (h[n-1] = 0)."""
+    import paper_2509_22684_gb300 as zk
+    F = fld.BLS12_381
+    L = 16
+    A, B = (uniform_elements(F.r, 1 << L, s) for s in (3101, 3102))
+    a, b = to_dev(A), to_dev(B)
+    c = zk.field_op(F.name, "mul", a, b)
+    h = to_host(zk.groth16_h(F.name, L, a, b, c, fused=True))
+    assert not h[-1].any()
+    assert h[:-1].any()
+
+
+def test_bounded_wait_reports_timeout():
+    import torch
+    from paper_2509_22684_gb300 import _native as N
+    st = N.lib().zkntt_selftest_timeout(20, None)
+    assert st == N.ETIMEOUT
+    # the context is still usable afterwards
+    F = fld.BLS12_381
+    X, x = rand_dev(F, 12, 1)
+    import paper_2509_22684_gb300 as zk
+    with zk.Plan(F.name, 12) as p:
+        assert np.array_equal(to_host(p.execute(x)), ref.ntt_mont(F, X))
+    zk.sync_status()

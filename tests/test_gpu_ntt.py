@@ -1,0 +1,151 @@
+"""GPU transform parity against the oracle: every direction and coset kind,
+both fields, single-pass and multi-pass schedules, both twiddle modes, forced
+digit splits, in place and out of place.  Bit-exact comparison throughout."""
+import numpy as np
+import pytest
+
+from oracle import cpu
+from oracle import field as fld
+from oracle import ntt_ref as ref
+
+from gpu_util import first_mismatch, rand_dev, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+FIELDS = [fld.BLS12_381, fld.BN254]
+KINDS = ["ntt", "intt", "coset_ntt", "coset_intt"]
+
+
+def _oracle(F, X, kind):
+    inverse = kind.endswith("intt")
+    sh = F.to_mont(F.g) if kind.startswith("coset") else None
+    if X.shape[0] <= 1 << 10:
+        return ref.ntt_mont(F, X, inverse=inverse, shift_mont=sh)
+    return cpu.ntt(F, X, inverse=inverse, shift_mont=sh)
+
+
+def _plan(F, L, kind, **kw):
+    import paper_2509_22684_gb300 as zk
+    inverse = kind.endswith("intt")
+    sh = F.to_mont(F.g) if kind.startswith("coset") else None
+    return zk.Plan(F.name, L, inverse=inverse, coset_shift=sh, **kw)
+
+
+@pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("L", list(range(1, 15)))
+def test_default_schedule(F, kind, L):
+    X, x = rand_dev(F, L, 1000 * L + 7)
+    with _plan(F, L, kind) as p:
+        y = p.execute(x)
+    got = to_host(y)
+    want = _oracle(F, X, kind)
+    assert np.array_equal(got, want), first_mismatch(got, want)
+
+
+@pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("mode", ["precomp", "otf"])
+@pytest.mark.parametrize("digits,cols", [
+    ((8, 8), None), ((4, 11), None), ((5, 6, 5), None), ((11, 5), (1, 8)),
+    ((3, 4, 5, 4), None), ((6, 10), (2, 2)), ((9, 7), (4, 4)), ((4, 4, 4, 4), (8, 8, 8, 8)),
+])
+def test_forced_splits(F, kind, mode, digits, cols):
+    L = sum(digits)
+    X, x = rand_dev(F, L, 77 + L)
+    with _plan(F, L, kind, twiddle_mode=mode, digits=digits, cols=cols) as p:
+        assert p.describe()["digits"] == list(digits)
+        y = p.execute(x)
+    got = to_host(y)
+    want = _oracle(F, X, kind)
+    assert np.array_equal(got, want), first_mismatch(got, want)
+
+
+@pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
+@pytest.mark.parametrize("L", [12, 17])
+def test_in_place_and_scratch(F, L):
+    import torch
+    X, x = rand_dev(F, L, 5)
+    want = _oracle(F, X, "coset_ntt")
+    with _plan(F, L, "coset_ntt") as p:
+        p.execute(x, x)   # in place
+        assert np.array_equal(to_host(x), want)
+        x2 = to_dev(X)
+        out = torch.empty_like(x2)
+        scr = torch.empty(max(1, p.scratch_bytes() // 4), dtype=torch.int32, device="cuda")
+        p.execute_scratch(x2, out, scr)
+        assert np.array_equal(to_host(out), want)
+
+
+@pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
+@pytest.mark.parametrize("L", [16, 20, 22])
+@pytest.mark.parametrize("kind", KINDS)
+def test_configured_sizes_full_vector(F, L, kind):
+    X, x = rand_dev(F, L, 2000 + L)
+    with _plan(F, L, kind) as p:
+        y = p.execute(x)
+    got = to_host(y)
+    want = _oracle(F, X, kind)
+    assert np.array_equal(got, want), first_mismatch(got, want)
+
+
+@pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
+@pytest.mark.parametrize("mode", ["precomp", "otf"])
+def test_2_24_full_vector(F, mode):
+    L = 24
+    X, x = rand_dev(F, L, 2024)
+    with _plan(F, L, "ntt", twiddle_mode=mode) as p:
+        y = p.execute(x)
+    got = to_host(y)
+    want = cpu.ntt(F, X)
+    assert np.array_equal(got, want), first_mismatch(got, want)
+
+
+@pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
+def test_2_26_sampled_outputs_and_round_trip(F):
+    """2^26: outputs at sampled k against the definition (Horner in the C
+    oracle), and inverse(forward(x)) == x over the whole vector."""
+    L = 26
+    X, x = rand_dev(F, L, 2026)
+    with _plan(F, L, "ntt") as p, _plan(F, L, "intt") as q:
+        y = p.execute(x)
+        z = q.execute(y)
+    got = to_host(y)
+    w = F.root(L)
+    for k in (0, 1, 3, (1 << L) - 1, 12345677):
+        assert int.from_bytes(got[k].tobytes(), "little") == cpu.eval_at(F, X, F.to_mont(pow(w, k, F.r)))
+    assert np.array_equal(to_host(z), X)
+
+
+def test_round_trip_config1():
+    """BLS12-381, n = 2^12, seed 1001: forward then inverse returns the input."""
+    F = fld.BLS12_381
+    X, x = rand_dev(F, 12, 1001)
+    with _plan(F, 12, "ntt") as p, _plan(F, 12, "intt") as q:
+        y = p.execute(x)
+        z = q.execute(y)
+    assert np.array_equal(to_host(y), ref.ntt_mont(F, X))
+    assert np.array_equal(to_host(z), X)
+
+
+def test_argument_errors():
+    import torch
+    import paper_2509_22684_gb300 as zk
+    from paper_2509_22684_gb300 import ZkNttError
+    with pytest.raises(ZkNttError):
+        zk.Plan("bls12_381_fr", 0)
+    with pytest.raises(ZkNttError):
+        zk.Plan("bn254_fr", 29)
+    with pytest.raises(ZkNttError):
+        zk.Plan("bls12_381_fr", 10, coset_shift=0)
+    with pytest.raises(ZkNttError):
+        zk.Plan("bls12_381_fr", 10, coset_shift=fld.BLS12_381.r)
+    with pytest.raises(ZkNttError):
+        zk.Plan("bls12_381_fr", 20, digits=(10, 9))
+    with zk.Plan("bls12_381_fr", 10) as p:
+        buf = torch.zeros((1 << 10) * 8 + 8, dtype=torch.int32, device="cuda")
+        mis = buf[1:1 + (1 << 10) * 8]   # 4-byte offset: misaligned
+        with pytest.raises(ZkNttError):
+            p.execute(mis, torch.empty_like(mis))
+        a = torch.zeros(((1 << 10) + 2) * 8, dtype=torch.int32, device="cuda")
+        with pytest.raises(ZkNttError):   # partial overlap
+            p.execute(a[:(1 << 10) * 8], a[16:16 + (1 << 10) * 8])
