@@ -128,6 +128,36 @@ zkntt_status zkntt_execute_scratch(zkntt_plan plan, const void *d_in, void *d_ou
  */
 zkntt_status zkntt_execute_host(zkntt_plan plan, const void *h_in, void *h_out, void *stream);
 
+/* Largest scratch zkntt_execute_noalloc can use: 32 MiB, i.e. transforms of up
+ * to 2^20 elements. */
+#define ZKNTT_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+
+/*
+ * zkntt_execute without any device allocation inside the call.  (The paper has
+ * no counterpart; this exists for callers of this library.)  It is meant for
+ * callers that must not allocate device memory while they run: for example a
+ * host application that reserves the device's memory for itself up front and
+ * does not let libraries call cudaMalloc, or a latency-critical loop that
+ * cannot afford the device-wide synchronisation an allocation may cause.
+ * The caller still passes the input and output vectors (and created the plan
+ * beforehand); multi-pass sizes use a scratch array of
+ * ZKNTT_NOALLOC_SCRATCH_BYTES that is a static device variable of this
+ * library, so every GPU that loads the library holds those 32 MiB until the
+ * process exits.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and keeps it; make that
+ *     first call before any stream capture.
+ *   - Plans whose scratch exceeds ZKNTT_NOALLOC_SCRATCH_BYTES (log_n > 20) are
+ *     rejected with ZKNTT_EINVAL before anything is enqueued.
+ *   - All calls on a device share the one array, which keeps whatever the last
+ *     call left in it (the transform writes every scratch element before reading
+ *     it, so nothing needs clearing).  Calls whose work can overlap on the GPU
+ *     -- on different streams, or from several host threads -- race on the
+ *     array; order them on one stream or synchronise between them.
+ * Arguments, layout, aliasing and asynchrony as for zkntt_execute.
+ */
+zkntt_status zkntt_execute_noalloc(zkntt_plan plan, const void *d_in, void *d_out, void *stream);
+
 /*
  * Run `count` independent transforms (each with its own plan; sizes, fields and
  * directions may differ) as ONE persistent kernel launch.  Work items (job,

@@ -56,6 +56,7 @@ SIGNATURES = {
     "zkntt_execute": [_vp, _vp, _vp, _vp],
     "zkntt_execute_scratch": [_vp, _vp, _vp, _vp, _sz, _vp],
     "zkntt_execute_host": [_vp, _vp, _vp, _vp],
+    "zkntt_execute_noalloc": [_vp, _vp, _vp, _vp],
     "zkntt_execute_batch": [ctypes.POINTER(_vp), ctypes.POINTER(IO), _i, _vp],
     "zkntt_groth16_h": [_i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp],
     "zkntt_status_str": [_i],

@@ -581,6 +581,30 @@ zkntt_status run_passes(const zkntt_plan_s *P, const void *in, void *out, void *
     return ZKNTT_OK;
 }
 
+// Scratch for zkntt_execute_noalloc: a file-scope device array, so that entry
+// point never allocates.  In host code `g_noalloc_scratch` only stands for the
+// symbol; its device address comes from cudaGetSymbolAddress, looked up once
+// per device (with that device current) and kept in a fixed table.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ZKNTT_NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+zkntt_status noalloc_scratch(void **out) {
+    int dev = 0;
+    ZK_CHECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return ZKNTT_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        ZK_CHECK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return ZKNTT_OK;
+}
+
 size_t scratch_bytes_of(const zkntt_plan_s *P) {
     return P->passes > 1 ? (size_t(32) << P->log_n) : 0;
 }
@@ -855,6 +879,20 @@ zkntt_status zkntt_execute_host(zkntt_plan plan, const void *h_in, void *h_out, 
     if (st == ZKNTT_OK) st = from_cuda(cudaMemcpyAsync(h_out, buf, bytes, cudaMemcpyDeviceToHost, s));
     zkntt_status st2 = from_cuda(cudaFreeAsync(buf, s));
     return st != ZKNTT_OK ? st : st2;
+}
+
+zkntt_status zkntt_execute_noalloc(zkntt_plan plan, const void *d_in, void *d_out, void *stream) {
+    if (!plan || bad_ptr(d_in) || bad_ptr(d_out)) return ZKNTT_EINVAL;
+    const size_t bytes = size_t(32) << plan->log_n;
+    if (partial_overlap(d_in, d_out, bytes)) return ZKNTT_EINVAL;
+    const size_t need = scratch_bytes_of(plan);
+    if (need > ZKNTT_NOALLOC_SCRATCH_BYTES) return ZKNTT_EINVAL;
+    void *scratch = nullptr;
+    if (need) {
+        zkntt_status st = noalloc_scratch(&scratch);
+        if (st != ZKNTT_OK) return st;
+    }
+    return run_passes(plan, d_in, d_out, scratch, static_cast<cudaStream_t>(stream));
 }
 
 zkntt_status zkntt_execute_batch(const zkntt_plan *plans, const zkntt_io *ptrs, int count,
