@@ -22,8 +22,9 @@ __global__ void gen_powers_kernel(uint4 *out, uint32_t count, const uint4 *hi, c
     }
 }
 
-// Inter-pass twiddle table in position order:
-//   out[lo * 2^K + d] = w^(lo * rev_K(d)) * fl[lo] * fd[d]
+// Inter-pass twiddle table, row-major by position d (so a tile of consecutive
+// columns lo reads consecutive entries):
+//   out[d * 2^lo_bits + lo] = w^(lo * rev_K(d)) * fl[lo] * fd[d]
 // with w^e = w_hi[e >> split] * w_lo[e & mask] (any scalar factor folded into
 // w_lo by the host).  fl / fd may be null.
 template <class F>
@@ -33,8 +34,8 @@ __global__ void gen_twiddle_kernel(uint4 *out, uint32_t K, uint32_t lo_bits, con
     const size_t total = size_t(1) << (lo_bits + K);
     for (size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
          idx += size_t(gridDim.x) * blockDim.x) {
-        uint32_t lo = uint32_t(idx >> K);
-        uint32_t d = uint32_t(idx & ((size_t(1) << K) - 1));
+        uint32_t d = uint32_t(idx >> lo_bits);
+        uint32_t lo = uint32_t(idx & ((size_t(1) << lo_bits) - 1));
         uint32_t e = lo * brev_bits(d, K);  // < 2^(lo_bits + K)
         uint32_t a[8], b[8];
         ldg_elem(a, w_hi + 2 * size_t(e >> split));

@@ -16,29 +16,11 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     return v;
 }
 
-// One out-of-line tile routine per (field, digit size): the persistent kernel
-// calls it through a switch, so each body is register-allocated on its own.
-template <class F, int K>
-__device__ __noinline__ void batch_tile(const PassArgs &a, uint4 *smem, uint32_t tile) {
-    run_tile<F, K>(a, smem, tile);
-}
-
+// One out-of-line tile routine per field, so each is register-allocated on
+// its own.
 template <class F>
-__device__ __forceinline__ void run_tile_k(const PassArgs &a, uint4 *smem, uint32_t K,
-                                           uint32_t tile) {
-    switch (K) {
-        case 1: batch_tile<F, 1>(a, smem, tile); break;
-        case 2: batch_tile<F, 2>(a, smem, tile); break;
-        case 3: batch_tile<F, 3>(a, smem, tile); break;
-        case 4: batch_tile<F, 4>(a, smem, tile); break;
-        case 5: batch_tile<F, 5>(a, smem, tile); break;
-        case 6: batch_tile<F, 6>(a, smem, tile); break;
-        case 7: batch_tile<F, 7>(a, smem, tile); break;
-        case 8: batch_tile<F, 8>(a, smem, tile); break;
-        case 9: batch_tile<F, 9>(a, smem, tile); break;
-        case 10: batch_tile<F, 10>(a, smem, tile); break;
-        default: batch_tile<F, 11>(a, smem, tile); break;
-    }
+__device__ __noinline__ void batch_tile(const PassArgs &a, uint4 *smem, uint32_t tile) {
+    run_tile<F>(a, smem, tile, pass_threads(a.K, a.log_cols));
 }
 
 // ctrl[0]: next work item, ctrl[1]: abort word; done[s]: tiles retired per
@@ -87,8 +69,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
         if (s_stop) break;
         const BatchSeg &sg = tab.seg[s_seg];
         const uint32_t tile = s_item - sg.first_item;
-        if (sg.field == 0) run_tile_k<FrBLS12_381>(sg.a, smem, sg.K, tile);
-        else run_tile_k<FrBN254>(sg.a, smem, sg.K, tile);
+        if (sg.field == 0) batch_tile<FrBLS12_381>(sg.a, smem, tile);
+        else batch_tile<FrBN254>(sg.a, smem, tile);
         // run_tile ends with a block barrier: every store of the tile is issued
         if (threadIdx.x == 0) {
             __threadfence();

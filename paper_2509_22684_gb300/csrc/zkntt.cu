@@ -236,12 +236,9 @@ zkntt_status device_info(DeviceInfo **out) {
     DeviceInfo &d = g_devices[dev];
     if (!d.init) {
         ZK_CHECK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
-        for (int f = 0; f < 2; f++) {
-            const FieldKernels &k = field_kernels(f);
-            for (int K = 1; K <= MAX_DIGIT_BITS; K++)
-                ZK_CHECK(cudaFuncSetAttribute(k.pass[K], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              64 * 1024));
-        }
+        for (int f = 0; f < 2; f++)
+            ZK_CHECK(cudaFuncSetAttribute(field_kernels(f).pass,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
         ZK_CHECK(cudaFuncSetAttribute(batch_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       64 * 1024));
         ZK_CHECK(cudaMalloc(&d.status, sizeof(uint32_t)));
@@ -266,7 +263,7 @@ struct PassPlan {
     int threads = 0, grid = 0;
     uint32_t num_tiles = 0;
     size_t smem = 0;
-    uint4 *w_sub = nullptr, *tw = nullptr, *w_hi = nullptr, *w_lo = nullptr, *fl = nullptr,
+    uint4 *w_stage = nullptr, *tw = nullptr, *w_hi = nullptr, *w_lo = nullptr, *fl = nullptr,
           *fd = nullptr;
     int tw_bits = 0, split_bits = 0;
 };
@@ -452,20 +449,28 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
         ps.log_cols = lc;
         ps.num_tiles = last ? (uint32_t(1) << (ps.hi_bits - lc))
                             : (uint32_t(1) << (ps.hi_bits + ps.lo_bits - lc));
-        const int T = ps.K >= 3 ? (1 << (ps.K - 3)) : 1;
-        ps.threads = T << lc;
+        ps.threads = int(pass_threads(uint32_t(ps.K), uint32_t(lc)));
         ps.smem = size_t(32) << (ps.K + lc);
         int nb = 0;
         ZK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &nb, field_kernels(P->field).pass[ps.K], ps.threads, ps.smem));
+            &nb, field_kernels(P->field).pass, ps.threads, ps.smem));
         nb = std::max(nb, 1);
         ps.grid = int(std::min<uint64_t>(ps.num_tiles, uint64_t(nb) * dev->sms));
 
-        // sub-transform twiddles w_N^e, e < N/2
+        // sub-transform twiddles, stage-major: stage s holds w_N^(j 2^s) for
+        // j < N / 2^(s+1) at offset N - 2^(K-s)
         const E8 wn_i = hpow(F, w, uint64_t(1) << ps.hi_bits);          // root of order n_i
         const E8 wN = hpow(F, wn_i, uint64_t(1) << ps.lo_bits);         // root of order N_i
-        st = upload(P, &ps.w_sub, powers(F, wN, std::max<size_t>(1, (size_t(1) << ps.K) / 2), F.one));
-        if (st != ZKNTT_OK) return st;
+        {
+            const size_t N = size_t(1) << ps.K;
+            std::vector<E8> all = powers(F, wN, std::max<size_t>(1, N / 2), F.one);
+            std::vector<E8> st_tab;
+            st_tab.reserve(N);
+            for (int sidx = 0; sidx < ps.K; sidx++)
+                for (size_t j = 0; j < (N >> (sidx + 1)); j++) st_tab.push_back(all[j << sidx]);
+            st = upload(P, &ps.w_stage, st_tab);
+            if (st != ZKNTT_OK) return st;
+        }
 
         // per-row coset-inverse factor for this digit: g^-(rev(d) * 2^hi_bits)
         std::vector<E8> phi;
@@ -532,7 +537,8 @@ PassArgs pass_args(const zkntt_plan_s *P, int i, const void *in, void *out) {
     memset(&a, 0, sizeof a);
     a.in = static_cast<const uint4 *>(in);
     a.out = static_cast<uint4 *>(out);
-    a.w_sub = ps.w_sub;
+    a.w_stage = ps.w_stage;
+    a.K = uint32_t(ps.K);
     a.tw = ps.tw;
     a.w_hi = ps.w_hi;
     a.w_lo = ps.w_lo;
@@ -576,7 +582,7 @@ zkntt_status run_passes(const zkntt_plan_s *P, const void *in, void *out, void *
         PassArgs a = pass_args(P, i, src, dst);
         void *args[] = {&a};
         const PassPlan &ps = P->ps[i];
-        ZK_CHECK(cudaLaunchKernel(kk.pass[ps.K], dim3(ps.grid), dim3(ps.threads), args, ps.smem, s));
+        ZK_CHECK(cudaLaunchKernel(kk.pass, dim3(ps.grid), dim3(ps.threads), args, ps.smem, s));
     }
     return ZKNTT_OK;
 }
