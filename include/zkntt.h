@@ -69,6 +69,7 @@ typedef struct {
     int digit_bits[4];     /* log2 sub-transform size per pass, top digit first; sum = log_n */
     int cols_per_cta[4];   /* columns per thread block per pass (1,2,4,8); 0 = planner's choice */
     int use_tuner;         /* 1 = consult the tuning cache (ZKNTT_TUNE_CACHE) */
+    int ilp;               /* butterflies each thread interleaves per stage step: 1 or 2; 0 = auto */
 } zkntt_plan_options;
 
 /*
@@ -227,6 +228,7 @@ typedef struct {
     int digit_bits[4];
     int cols_per_cta[4];
     int twiddle_mode;
+    int ilp;
     float ms;            /* median time of one transform with that schedule */
 } zkntt_tune_result;
 

@@ -59,7 +59,8 @@ class Plan:
     """One transform size / direction / coset on the current device."""
 
     def __init__(self, field, log_n: int, inverse: bool = False, coset_shift: int | None = None,
-                 twiddle_mode: str = "auto", digits=None, cols=None, use_tuner: bool = False):
+                 twiddle_mode: str = "auto", digits=None, cols=None, use_tuner: bool = False,
+                 ilp: int = 0):
         self.field = _field_id(field)
         self.log_n = int(log_n)
         self.inverse = bool(inverse)
@@ -74,6 +75,7 @@ class Plan:
             for i, c in enumerate(cols):
                 opts.cols_per_cta[i] = int(c)
         opts.use_tuner = int(use_tuner)
+        opts.ilp = int(ilp)
         shift = None if coset_shift is None else N.limbs_of(coset_shift)
         h = ctypes.c_void_p()
         N.check(N.lib().zkntt_plan_create_ex(ctypes.byref(h), self.field, self.log_n,
@@ -212,7 +214,8 @@ def tune(field, log_n: int, inverse: bool = False, max_candidates: int = 24) -> 
                                ctypes.byref(r)), "zkntt_tune")
     return {"passes": r.num_passes, "digits": list(r.digit_bits)[:r.num_passes],
             "cols": list(r.cols_per_cta)[:r.num_passes],
-            "twiddle_mode": {1: "precomp", 2: "otf"}.get(r.twiddle_mode, "auto"), "ms": r.ms}
+            "twiddle_mode": {1: "precomp", 2: "otf"}.get(r.twiddle_mode, "auto"), "ilp": r.ilp,
+            "ms": r.ms}
 
 
 def sync_status(stream=None) -> None:

@@ -26,7 +26,7 @@ class ZkNttError(RuntimeError):
 class PlanOptions(ctypes.Structure):
     _fields_ = [("twiddle_mode", ctypes.c_int), ("num_passes", ctypes.c_int),
                 ("digit_bits", ctypes.c_int * 4), ("cols_per_cta", ctypes.c_int * 4),
-                ("use_tuner", ctypes.c_int)]
+                ("use_tuner", ctypes.c_int), ("ilp", ctypes.c_int)]
 
 
 class IO(ctypes.Structure):
@@ -36,7 +36,7 @@ class IO(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("num_passes", ctypes.c_int), ("digit_bits", ctypes.c_int * 4),
                 ("cols_per_cta", ctypes.c_int * 4), ("twiddle_mode", ctypes.c_int),
-                ("ms", ctypes.c_float)]
+                ("ilp", ctypes.c_int), ("ms", ctypes.c_float)]
 
 
 _lib = None

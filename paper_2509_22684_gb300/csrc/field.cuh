@@ -117,38 +117,51 @@ __device__ __forceinline__ void sub(uint32_t r[8], const uint32_t a[8], const ui
 // ---------------------------------------------------------------------------
 // Montgomery product, CIOS with one 64-bit partial product per limb pair.
 //
-// Outer step i adds a * b_i to the running value t (t < 2r, nine limbs):
-//   P_j = a_j * b_i + t_j                (j = 0..7; fits 64 bits exactly)
-//   t   = P_0.lo, P_0.hi + P_1.lo, ..., P_6.hi + P_7.lo, P_7.hi + t_8
-// so each partial product is one wide multiply-add and the overlapping halves
-// are merged by a single add-with-carry chain.  The reduction step is the same
-// with m = t_0 r' mod 2^32 and Q_j = m r_j + t_j; Q_0.lo is zero by the choice
-// of m, so the merge also divides by 2^32.  Measured on GB300 this issues about
-// 430 instructions per product against 576 for separate mad.lo.cc / madc.hi.cc
-// chains (the 32-bit high-half multiplies occupy the multiply pipe as long as a
-// wide one).  With r < 2^255 (both fields) the bound t < 2r holds after every
-// step, so t_8 never carries out.
-__device__ __forceinline__ void merge_row(uint32_t t[9], const uint64_t P[8]) {
+// Outer step i adds a * b_i to the running value t (t < 2r, nine limbs): the
+// eight wide products P_j = a_j * b_i are independent; two add-with-carry
+// chains fold them in (t += P.lo at positions 0..7, then t += P.hi at
+// positions 1..8).  The reduction step forms Q_j = m r_j + t_j with
+// m = t_0 r' mod 2^32 -- a 64-bit multiply-add that cannot overflow -- and one
+// chain merges Q_j.hi with Q_{j+1}.lo; Q_0.lo is zero by the choice of m, so
+// that merge also divides by 2^32.
+//
+// Why this split: on GB300 the wide multiplies run on the heavy FMA datapath
+// at half rate, and a multiply-add whose 64-bit addend is a zero-extended
+// 32-bit value also needs a move on that datapath, while the add chains run on
+// the ALU pipe.  Using the addend form only in the reduction rows balances the
+// two pipes: about 405 instructions and 600 heavy-pipe cycles per warp-wide
+// product, against 576 instructions for separate mad.lo.cc / madc.hi.cc
+// chains (measured: 53 vs 43 G products/s for BLS12-381 F_r).  With r < 2^255
+// (both fields) t < 2r holds after every step, so t_8 never carries out.
+__device__ __forceinline__ void merge_product_row(uint32_t t[9], const uint64_t P[8]) {
     uint32_t lo[8], hi[8];
 #pragma unroll
     for (int j = 0; j < 8; j++) {
         lo[j] = uint32_t(P[j]);
         hi[j] = uint32_t(P[j] >> 32);
     }
-    t[0] = lo[0];
-    asm("add.cc.u32  %0, %8, %16;\n\t"
-        "addc.cc.u32 %1, %9, %17;\n\t"
-        "addc.cc.u32 %2, %10, %18;\n\t"
-        "addc.cc.u32 %3, %11, %19;\n\t"
-        "addc.cc.u32 %4, %12, %20;\n\t"
-        "addc.cc.u32 %5, %13, %21;\n\t"
-        "addc.cc.u32 %6, %14, %22;\n\t"
-        "addc.u32    %7, %15, %7;"
-        : "=r"(t[1]), "=r"(t[2]), "=r"(t[3]), "=r"(t[4]), "=r"(t[5]), "=r"(t[6]), "=r"(t[7]),
-          "+r"(t[8])
-        : "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]),
-          "r"(hi[7]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]),
-          "r"(lo[7]));
+    asm("add.cc.u32  %0, %0, %9;\n\t"
+        "addc.cc.u32 %1, %1, %10;\n\t"
+        "addc.cc.u32 %2, %2, %11;\n\t"
+        "addc.cc.u32 %3, %3, %12;\n\t"
+        "addc.cc.u32 %4, %4, %13;\n\t"
+        "addc.cc.u32 %5, %5, %14;\n\t"
+        "addc.cc.u32 %6, %6, %15;\n\t"
+        "addc.cc.u32 %7, %7, %16;\n\t"
+        "addc.u32    %8, %8, 0;\n\t"
+        "add.cc.u32  %1, %1, %17;\n\t"
+        "addc.cc.u32 %2, %2, %18;\n\t"
+        "addc.cc.u32 %3, %3, %19;\n\t"
+        "addc.cc.u32 %4, %4, %20;\n\t"
+        "addc.cc.u32 %5, %5, %21;\n\t"
+        "addc.cc.u32 %6, %6, %22;\n\t"
+        "addc.cc.u32 %7, %7, %23;\n\t"
+        "addc.u32    %8, %8, %24;"
+        : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]),
+          "+r"(t[7]), "+r"(t[8])
+        : "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]),
+          "r"(lo[7]), "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]),
+          "r"(hi[6]), "r"(hi[7]));
 }
 
 // reduction merge: t'_j = Q_j.hi + Q_{j+1}.lo (j < 7), t'_7 = Q_7.hi + t_8
@@ -188,8 +201,8 @@ __device__ __forceinline__ void mul(uint32_t r[8], const uint32_t a[8], const ui
     for (int i = 0; i < 8; i++) {
         uint64_t X[8];
 #pragma unroll
-        for (int j = 0; j < 8; j++) X[j] = uint64_t(a[j]) * bb[i] + t[j];
-        merge_row(t, X);
+        for (int j = 0; j < 8; j++) X[j] = uint64_t(a[j]) * bb[i];
+        merge_product_row(t, X);
         // m = t_0 r' mod 2^32 (for BLS12-381 F_r, r' = 2^32 - 1 and r_0 = 1,
         // r_1 = 2^32 - 1: the compiler turns those products into adds)
         const uint32_t m = t[0] * F::RP;

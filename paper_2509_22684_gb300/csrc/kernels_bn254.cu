@@ -8,7 +8,7 @@ namespace zkntt {
 const FieldKernels &kernels_bn254() {
     using F = FrBN254;
     static const FieldKernels k = {
-        (const void *)&ntt_pass_kernel<F>,
+        {nullptr, (const void *)&ntt_pass_kernel<F, 1>, (const void *)&ntt_pass_kernel<F, 2>},
         (const void *)&gen_powers_kernel<F>,
         (const void *)&gen_twiddle_kernel<F>,
         (const void *)&field_op_kernel<F>,

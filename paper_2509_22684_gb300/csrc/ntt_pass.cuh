@@ -157,7 +157,7 @@ __device__ __forceinline__ bool out_factor(uint32_t f[8], const PassArgs &a, uin
 
 // Process one tile with `nthreads` threads of the block (threads at or beyond
 // nthreads only take part in the barriers).
-template <class F>
+template <class F, int ILP>
 __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_t tile,
                                          uint32_t nthreads) {
     const uint32_t K = a.K, lc = a.log_cols;
@@ -207,26 +207,41 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
     }
     __syncthreads();
 
-    // ---- stages 0 .. K-3: radix-2 butterflies through shared memory
+    // ---- stages 0 .. K-3: radix-2 butterflies through shared memory.  Each
+    // thread takes ILP independent butterflies per step (every thread owns at
+    // least two per stage: nthreads <= C*N/4), so the carry chains and loads of
+    // one overlap with the other's product.
     for (uint32_t s = 0; s + 2 < K; s++) {
         const uint32_t lh = K - 1 - s;
         const uint32_t h = 1u << lh;
         const uint4 *ws = a.w_stage + 2 * size_t(N - 2 * h);
-        for (uint32_t bg = tid; active && bg < (CN >> 1); bg += nthreads) {
-            const uint32_t cc = bg >> (K - 1);
-            const uint32_t b = bg & ((N >> 1) - 1);
-            const uint32_t j = b & (h - 1);
-            const uint32_t i0 = ((b >> lh) << (lh + 1)) | j;
-            const uint32_t s0 = smem_slot(cc, i0, K, lc), s1 = smem_slot(cc, i0 + h, K, lc);
-            uint32_t x[8], y[8], w[8], t[8];
-            lds_elem(x, s_lo, s_hi, s0);
-            lds_elem(y, s_lo, s_hi, s1);
-            ldg_elem(w, ws + 2 * size_t(j));
-            sub<F>(t, x, y);
-            add<F>(x, x, y);
-            mul<F>(y, t, w);
-            sts_elem(s_lo, s_hi, s0, x);
-            sts_elem(s_lo, s_hi, s1, y);
+        for (uint32_t bg = tid; active && bg < (CN >> 1); bg += ILP * nthreads) {
+            uint32_t x[ILP][8], y[ILP][8], w[ILP][8], t[ILP][8], s0[ILP], s1[ILP];
+#pragma unroll
+            for (int k = 0; k < ILP; k++) {
+                const uint32_t bk = bg + k * nthreads;
+                const uint32_t cc = bk >> (K - 1);
+                const uint32_t b = bk & ((N >> 1) - 1);
+                const uint32_t j = b & (h - 1);
+                const uint32_t i0 = ((b >> lh) << (lh + 1)) | j;
+                s0[k] = smem_slot(cc, i0, K, lc);
+                s1[k] = smem_slot(cc, i0 + h, K, lc);
+                lds_elem(x[k], s_lo, s_hi, s0[k]);
+                lds_elem(y[k], s_lo, s_hi, s1[k]);
+                ldg_elem(w[k], ws + 2 * size_t(j));
+            }
+#pragma unroll
+            for (int k = 0; k < ILP; k++) {
+                sub<F>(t[k], x[k], y[k]);
+                add<F>(x[k], x[k], y[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < ILP; k++) mul<F>(y[k], t[k], w[k]);
+#pragma unroll
+            for (int k = 0; k < ILP; k++) {
+                sts_elem(s_lo, s_hi, s0[k], x[k]);
+                sts_elem(s_lo, s_hi, s1[k], y[k]);
+            }
         }
         __syncthreads();
     }
@@ -299,11 +314,13 @@ __host__ __device__ constexpr uint32_t pass_threads(uint32_t K, uint32_t lc) {
                : 256u;
 }
 
-template <class F>
-__global__ void __launch_bounds__(256, 3) ntt_pass_kernel(const PassArgs a) {
+// ILP = independent butterflies per thread per stage step (1 or 2); the
+// register budget follows: 3 blocks of 256 threads per SM for 1, 2 for 2.
+template <class F, int ILP>
+__global__ void __launch_bounds__(256, ILP == 1 ? 3 : 2) ntt_pass_kernel(const PassArgs a) {
     extern __shared__ uint4 smem[];
     for (uint32_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x)
-        run_tile<F>(a, smem, tile, blockDim.x);
+        run_tile<F, ILP>(a, smem, tile, blockDim.x);
 }
 
 }  // namespace zkntt

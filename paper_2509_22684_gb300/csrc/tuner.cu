@@ -43,7 +43,7 @@ const char *cache_path() {
 }
 
 // one entry per line:
-// {"gpu":"NAME","field":F,"log_n":L,"dir":D,"passes":P,"digits":[a,b,c,d],"log_cols":[a,b,c,d],"mode":M,"ms":T}
+// {"gpu":"NAME","field":F,"log_n":L,"dir":D,"passes":P,"digits":[a,b,c,d],"log_cols":[a,b,c,d],"mode":M,"ilp":I,"ms":T}
 void load_locked() {
     if (g_loaded) return;
     g_loaded = true;
@@ -64,11 +64,11 @@ void load_locked() {
         memcpy(name, q, end - q);
         int n = sscanf(end + 1,
                        ",\"field\":%d,\"log_n\":%d,\"dir\":%d,\"passes\":%d,\"digits\":[%d,%d,%d,%d],"
-                       "\"log_cols\":[%d,%d,%d,%d],\"mode\":%d,\"ms\":%lf",
+                       "\"log_cols\":[%d,%d,%d,%d],\"mode\":%d,\"ilp\":%d,\"ms\":%lf",
                        &field, &L, &dir, &e.passes, &e.digits[0], &e.digits[1], &e.digits[2],
                        &e.digits[3], &e.log_cols[0], &e.log_cols[1], &e.log_cols[2], &e.log_cols[3],
-                       &e.mode, &e.ms);
-        if (n == 14) g_cache[{std::string(name), field, L, dir}] = e;
+                       &e.mode, &e.ilp, &e.ms);
+        if (n == 15) g_cache[{std::string(name), field, L, dir}] = e;
     }
     fclose(f);
 }
@@ -96,9 +96,10 @@ void tuner_store(int field, int log_n, int dir, const TuneEntry &e) {
     if (!f) return;
     fprintf(f,
             "{\"gpu\":\"%s\",\"field\":%d,\"log_n\":%d,\"dir\":%d,\"passes\":%d,\"digits\":[%d,%d,%d,%d],"
-            "\"log_cols\":[%d,%d,%d,%d],\"mode\":%d,\"ms\":%.6f}\n",
+            "\"log_cols\":[%d,%d,%d,%d],\"mode\":%d,\"ilp\":%d,\"ms\":%.6f}\n",
             name.c_str(), field, log_n, dir, e.passes, e.digits[0], e.digits[1], e.digits[2],
-            e.digits[3], e.log_cols[0], e.log_cols[1], e.log_cols[2], e.log_cols[3], e.mode, e.ms);
+            e.digits[3], e.log_cols[0], e.log_cols[1], e.log_cols[2], e.log_cols[3], e.mode, e.ilp,
+            e.ms);
     fclose(f);
 }
 
@@ -147,11 +148,13 @@ extern "C" zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, 
         splits(log_n, p, sp);
         for (auto &d : sp)
             for (int mode : {ZKNTT_TWIDDLE_PRECOMP, ZKNTT_TWIDDLE_OTF})
+                for (int ilp : {1, 2})
                 for (int cap = 3; cap >= 1; cap--) {
                     if (p == 1 && (mode == ZKNTT_TWIDDLE_OTF || cap != 3)) continue;
                     Cand c;
                     memset(&c.o, 0, sizeof c.o);
                     c.o.twiddle_mode = mode;
+                    c.o.ilp = ilp;
                     c.o.num_passes = p;
                     int hi = 0;
                     for (int i = 0; i < p; i++) {
@@ -224,6 +227,7 @@ extern "C" zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, 
                 bestE.log_cols[i] = i < bestE.passes ? l : -1;
             }
             bestE.mode = cands[ci].o.twiddle_mode;
+            bestE.ilp = cands[ci].o.ilp;
             bestE.ms = med;
         }
     }
@@ -243,6 +247,7 @@ extern "C" zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, 
             best->cols_per_cta[i] = bestE.log_cols[i] >= 0 ? (1 << bestE.log_cols[i]) : 0;
         }
         best->twiddle_mode = bestE.mode;
+        best->ilp = bestE.ilp;
         best->ms = float(bestE.ms);
     }
     return ZKNTT_OK;

@@ -15,6 +15,7 @@ struct TuneEntry {
     int digits[4] = {0, 0, 0, 0};
     int log_cols[4] = {-1, -1, -1, -1};
     int mode = 0;
+    int ilp = 0;
     double ms = 0.0;
 };
 

@@ -237,8 +237,9 @@ zkntt_status device_info(DeviceInfo **out) {
     if (!d.init) {
         ZK_CHECK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
         for (int f = 0; f < 2; f++)
-            ZK_CHECK(cudaFuncSetAttribute(field_kernels(f).pass,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+            for (int ilp = 1; ilp <= 2; ilp++)
+                ZK_CHECK(cudaFuncSetAttribute(field_kernels(f).pass[ilp],
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
         ZK_CHECK(cudaFuncSetAttribute(batch_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       64 * 1024));
         ZK_CHECK(cudaMalloc(&d.status, sizeof(uint32_t)));
@@ -259,7 +260,7 @@ zkntt_status device_info(DeviceInfo **out) {
 
 // ---------------------------------------------------------------------------
 struct PassPlan {
-    int K = 0, lo_bits = 0, hi_bits = 0, log_cols = 0;
+    int K = 0, lo_bits = 0, hi_bits = 0, log_cols = 0, ilp = 1;
     int threads = 0, grid = 0;
     uint32_t num_tiles = 0;
     size_t smem = 0;
@@ -336,6 +337,9 @@ void default_digits(int L, int *passes, int k[4]) {
     }
 }
 
+// interleaved butterflies per thread in the stage loop (planner default)
+constexpr int DEFAULT_ILP = 1;
+
 int default_log_cols(int K, int span_bits) {
     // tile of C x 2^K elements, at most 2^11 elements (64 KiB); C <= 8 and
     // C <= the number of columns the pass has (2^span_bits)
@@ -388,6 +392,7 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
     // ---- schedule
     int k[4] = {0, 0, 0, 0}, cols[4] = {-1, -1, -1, -1};
     int mode = ZKNTT_TWIDDLE_AUTO;
+    int ilp = DEFAULT_ILP;
     default_digits(L, &P->passes, k);
     if (opts && opts->use_tuner) {
         TuneEntry te;
@@ -398,6 +403,7 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
                 cols[i] = te.log_cols[i];
             }
             mode = te.mode;
+            if (te.ilp == 1 || te.ilp == 2) ilp = te.ilp;
         }
     }
     if (opts && opts->num_passes > 0) {
@@ -415,6 +421,10 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
         }
     }
     if (opts && opts->twiddle_mode) mode = opts->twiddle_mode;
+    if (opts && opts->ilp) {
+        if (opts->ilp != 1 && opts->ilp != 2) return ZKNTT_EINVAL;
+        ilp = opts->ilp;
+    }
     if (mode != ZKNTT_TWIDDLE_OTF) mode = ZKNTT_TWIDDLE_PRECOMP;
     P->mode = mode;
     const int p = P->passes;
@@ -447,13 +457,14 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
             lc = cols[i];
         }
         ps.log_cols = lc;
+        ps.ilp = ilp;
         ps.num_tiles = last ? (uint32_t(1) << (ps.hi_bits - lc))
                             : (uint32_t(1) << (ps.hi_bits + ps.lo_bits - lc));
         ps.threads = int(pass_threads(uint32_t(ps.K), uint32_t(lc)));
         ps.smem = size_t(32) << (ps.K + lc);
         int nb = 0;
         ZK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &nb, field_kernels(P->field).pass, ps.threads, ps.smem));
+            &nb, field_kernels(P->field).pass[ps.ilp], ps.threads, ps.smem));
         nb = std::max(nb, 1);
         ps.grid = int(std::min<uint64_t>(ps.num_tiles, uint64_t(nb) * dev->sms));
 
@@ -582,7 +593,7 @@ zkntt_status run_passes(const zkntt_plan_s *P, const void *in, void *out, void *
         PassArgs a = pass_args(P, i, src, dst);
         void *args[] = {&a};
         const PassPlan &ps = P->ps[i];
-        ZK_CHECK(cudaLaunchKernel(kk.pass, dim3(ps.grid), dim3(ps.threads), args, ps.smem, s));
+        ZK_CHECK(cudaLaunchKernel(kk.pass[ps.ilp], dim3(ps.grid), dim3(ps.threads), args, ps.smem, s));
     }
     return ZKNTT_OK;
 }

@@ -149,3 +149,18 @@ def test_argument_errors():
         a = torch.zeros(((1 << 10) + 2) * 8, dtype=torch.int32, device="cuda")
         with pytest.raises(ZkNttError):   # partial overlap
             p.execute(a[:(1 << 10) * 8], a[16:16 + (1 << 10) * 8])
+
+
+@pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("digits,cols", [((8, 8), None), ((5, 6, 5), None), ((11, 5), (1, 8)),
+                                         ((4, 4, 4, 4), (8, 8, 8, 8)), ((10,), None), ((3,), None)])
+def test_interleaved_butterflies(F, kind, digits, cols):
+    """Two butterflies per thread per stage step (ilp=2) gives the same result."""
+    L = sum(digits)
+    X, x = rand_dev(F, L, 99 + L)
+    with _plan(F, L, kind, digits=digits, cols=cols, ilp=2) as p:
+        y = p.execute(x)
+    got = to_host(y)
+    want = _oracle(F, X, kind)
+    assert np.array_equal(got, want), first_mismatch(got, want)
