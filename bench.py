@@ -147,11 +147,8 @@ def barrier(world):
 def max_over_ranks(world, value: float) -> float:
     if world == 1:
         return value
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2509_22684_gb300.replicas import max_over_ranks as mor
+    return mor(value, device="cuda")
 
 
 def cpu_oracle_rate(field: str, log_n: int, budget_s: float, X=None):
@@ -240,8 +237,36 @@ def extras(zk, torch, field: str, stream, peak_imad: float, hbm_gbs: float) -> d
             f()
         ms = timed(f, stream, 10) / 10
         g16["fused_ms" if fused else "separate_ms"] = round(ms, 4)
+    gs = torch.cuda.Stream()
+    graph = zk.Groth16Graph(field, L, a, b, c, h, scr, stream=gs)
+    f = lambda: graph.launch(stream=stream)
+    for _ in range(3):
+        f()
+    g16["graph_ms"] = round(timed(f, stream, 10) / 10, 4)
+    graph.close()
     g16["speedup"] = round(g16["separate_ms"] / g16["fused_ms"], 3)
+    g16["graph_speedup"] = round(g16["separate_ms"] / g16["graph_ms"], 3)
     out["groth16_2^22"] = g16
+    # small Groth16 sizes, where launch overhead matters: separate vs fused graph
+    small = {}
+    for Ls in (12, 16, 20):
+        a2, b2, c2 = (torch.from_numpy(uniform_elements(F_r, 1 << Ls, s).view(np.int32)).cuda()
+                      for s in (3001, 3002, 3003))
+        h2 = torch.empty_like(a2)
+        s2 = torch.empty((3 << Ls, 8), dtype=torch.int32, device="cuda")
+        sep = lambda: zk.groth16_h(field, Ls, a2, b2, c2, h=h2, scratch=s2, fused=False, stream=stream)
+        for _ in range(3):
+            sep()
+        ms_sep = timed(sep, stream, 20) / 20
+        gr = zk.Groth16Graph(field, Ls, a2, b2, c2, h2, s2, stream=gs)
+        fg = lambda: gr.launch(stream=stream)
+        for _ in range(3):
+            fg()
+        ms_g = timed(fg, stream, 20) / 20
+        gr.close()
+        small[f"2^{Ls}"] = {"separate_ms": round(ms_sep, 4), "graph_ms": round(ms_g, 4),
+                            "speedup": round(ms_sep / ms_g, 3)}
+    out["groth16_small"] = small
     del a, b, c, h, scr
     # 64 uneven transforms: persistent batch vs one call per transform
     jobs = batch_jobs(4000, count=64, lmin=10, lmax=20)
@@ -270,6 +295,50 @@ def extras(zk, torch, field: str, stream, peak_imad: float, hbm_gbs: float) -> d
     for p in plans:
         p.close()
     return out
+
+
+def serve_bench(zk, torch, field: str, n_requests: int, load: float) -> dict:
+    """Served NTT stream: Poisson arrivals, log_n uniform on 12..24, kinds
+    uniform over {NTT, iNTT, coset NTT, coset iNTT}; offered load = `load` x the
+    measured serial capacity; continuous batching vs serial plain execution on
+    the same trace."""
+    import numpy as np
+    from paper_2509_22684_gb300.serve import Engine, GpuExecutor, Request, serve_serial
+    from workloads import KINDS, poisson_trace, uniform_elements
+    F_r = FIELD_R[field]
+    sizes = range(12, 25)
+    pool = {(field, L): torch.from_numpy(uniform_elements(F_r, 1 << L, 5000 + L).view(np.int32)).cuda()
+            for L in sizes}
+    ex = GpuExecutor(streams=2, input_pool=pool, keep_outputs=False)
+    cur = torch.cuda.current_stream()
+    svc = {}
+    for L in sizes:
+        for kind in KINDS:
+            ex.plan(field, L, kind)
+        p = ex.plan(field, L, "ntt")
+        x = pool[(field, L)]
+        y = torch.empty_like(x)
+        for _ in range(2):
+            p.execute(x, y, stream=cur)
+        svc[L] = timed(lambda: p.execute(x, y, stream=cur), cur, 5) / 5 / 1e3
+    mean_svc = sum(svc.values()) / len(svc)
+    rate = load / mean_svc
+    trace = poisson_trace(5000, n_requests, rate, 12, 24)
+    mk = lambda: [Request(i, q.arrival_s, field, q.log_n, q.kind) for i, q in enumerate(trace)]
+    eng = Engine(ex, budget_bytes=int(torch.cuda.mem_get_info()[0] * 0.5), streams=2, max_batch_jobs=64)
+    _, st = eng.run(mk())
+
+    def run_one(r):
+        x = pool[(r.field, r.log_n)]
+        ex.plan(r.field, r.log_n, r.kind).execute(x, torch.empty_like(x), stream=cur)
+        cur.synchronize()
+    _, ser = serve_serial(mk(), run_one)
+    ex.close()
+    return {"requests": n_requests, "offered_rate_per_s": round(rate, 1), "load": load,
+            "serial_capacity_per_s": round(1 / mean_svc, 1),
+            "batched": st.as_dict(), "serial": ser.as_dict(),
+            "p99_speedup": round(ser.p99_ms / st.p99_ms, 3),
+            "throughput_ratio": round(st.melem_s / ser.melem_s, 3)}
 
 
 def run_ours(args, world, rank, local):
@@ -373,6 +442,7 @@ def run_ours(args, world, rank, local):
                                   "sample": f"C oracle (oracle/cpu_ntt.c) forward NTT 2^{L}, {reps} run(s), {el:.1f} s"}
     if rank == 0 and not args.no_extras:
         result["extras"] = extras(zk, torch, field, stream, peak_imad, hbm_gbs)
+        result["extras"]["serving"] = serve_bench(zk, torch, field, args.serve_requests, args.serve_load)
     if rank == 0:
         print(json.dumps(result), flush=True)
 
@@ -434,6 +504,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-load", type=float, default=0.8)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -172,6 +172,23 @@ zkntt_status zkntt_execute_batch(const zkntt_plan *plans, const zkntt_io *ptrs, 
                                  void *stream);
 
 /*
+ * As zkntt_execute_batch, for serving: transforms are scheduled shortest
+ * first, each one's passes back to back, and when transform i has completed on
+ * the device the launch stores `epoch` into d_flags[i] with a system-scope
+ * release, so a host thread polling host-mapped memory (zkntt_flags_create)
+ * sees each result as soon as it is ready instead of at the end of the launch.
+ * d_flags: count words of device-accessible memory; the caller picks a fresh
+ * epoch per launch and may not reuse a slot before its flag is seen.
+ */
+zkntt_status zkntt_execute_batch_signal(const zkntt_plan *plans, const zkntt_io *ptrs, int count,
+                                        uint32_t *d_flags, uint32_t epoch, void *stream);
+
+/* Pinned host words that the device can write (zero-copy): host_view for
+ * polling, device_view for zkntt_execute_batch_signal.  Zero-initialised. */
+zkntt_status zkntt_flags_create(int count, uint32_t **host_view, uint32_t **device_view);
+zkntt_status zkntt_flags_destroy(uint32_t *host_view);
+
+/*
  * Groth16 H polynomial (Fig. 2; Section IV-A: seven NTT operations):
  *   a' = iNTT(a), b' = iNTT(b), c' = iNTT(c);
  *   A = cosetNTT_g(a'), B = cosetNTT_g(b'), C = cosetNTT_g(c');
@@ -186,6 +203,23 @@ zkntt_status zkntt_execute_batch(const zkntt_plan *plans, const zkntt_io *ptrs, 
 zkntt_status zkntt_groth16_h(zkntt_field field, int log_n, const void *d_a, const void *d_b,
                              const void *d_c, void *d_h, void *d_scratch, int fused,
                              void *stream);
+
+/*
+ * The fused Groth16 H sequence captured once into a CUDA graph: the capture
+ * records the persistent launch and its stream-ordered scratch allocations
+ * for these exact buffers; each zkntt_graph_launch replays it on `stream`
+ * with no host-side work per transform.  `stream` must be a created stream
+ * (not NULL) and idle during the call; the first call for a (field, log_n)
+ * also builds the transform plans before capturing.  The buffers must stay
+ * valid for the graph's lifetime.
+ */
+typedef struct zkntt_graph_s *zkntt_graph;
+
+zkntt_status zkntt_groth16_graph_create(zkntt_graph *out, zkntt_field field, int log_n,
+                                        const void *d_a, const void *d_b, const void *d_c, void *d_h,
+                                        void *d_scratch, void *stream);
+zkntt_status zkntt_graph_launch(zkntt_graph graph, void *stream);
+zkntt_status zkntt_graph_destroy(zkntt_graph graph);
 
 /* Static text for a status code. */
 const char *zkntt_status_str(zkntt_status status);

@@ -15,7 +15,8 @@ import torch
 from . import _native as N
 from ._native import ZkNttError, FIELDS, TWIDDLE_MODES
 
-__all__ = ["Plan", "ZkNttError", "FIELDS", "execute_batch", "groth16_h", "field_info",
+__all__ = ["Plan", "ZkNttError", "FIELDS", "execute_batch", "execute_batch_signal",
+           "CompletionFlags", "groth16_h", "Groth16Graph", "field_info",
            "field_op", "pointwise", "tune", "sync_status", "mulbench", "new_vector"]
 
 
@@ -175,6 +176,59 @@ def execute_batch(plans, inputs, outputs, stream=None) -> None:
             "zkntt_execute_batch")
 
 
+class CompletionFlags:
+    """Pinned host words the device writes when a transform of a signalled
+    batch completes (zero-copy; the host polls without synchronising)."""
+
+    def __init__(self, count: int):
+        h = ctypes.c_void_p()
+        d = ctypes.c_void_p()
+        N.check(N.lib().zkntt_flags_create(int(count), ctypes.byref(h), ctypes.byref(d)),
+                "zkntt_flags_create")
+        self.count = int(count)
+        self.host = h
+        self.device = d
+        self.view = (ctypes.c_uint32 * self.count).from_address(h.value)
+
+    def __getitem__(self, i: int) -> int:
+        return self.view[i]
+
+    def close(self):
+        if getattr(self, "host", None) is not None:
+            N.lib().zkntt_flags_destroy(self.host)
+            self.host = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def execute_batch_signal(plans, inputs, outputs, flags: CompletionFlags, slots, epoch: int,
+                         stream=None) -> None:
+    """As execute_batch, shortest transforms first; transform i stores `epoch`
+    into flags[slots[i]] when it completes.  `slots` must be consecutive
+    (slots[i] = slots[0] + i) within the flag array."""
+    count = len(plans)
+    if not (len(inputs) == len(outputs) == len(slots) == count):
+        raise ValueError("length mismatch")
+    base = slots[0]
+    if list(slots) != list(range(base, base + count)) or base + count > flags.count:
+        raise ValueError("slots must be a consecutive range inside the flag array")
+    hs = (ctypes.c_void_p * count)(*[p.handle.value for p in plans])
+    ios = (N.IO * count)()
+    for i in range(count):
+        plans[i]._check_vec(inputs[i])
+        plans[i]._check_vec(outputs[i])
+        ios[i].d_in = _ptr(inputs[i]).value
+        ios[i].d_out = _ptr(outputs[i]).value
+    dptr = ctypes.c_void_p(flags.device.value + 4 * base)
+    N.check(N.lib().zkntt_execute_batch_signal(hs, ios, count, dptr, ctypes.c_uint32(epoch),
+                                               _stream_handle(stream)),
+            "zkntt_execute_batch_signal")
+
+
 def groth16_h(field, log_n: int, a, b, c, h=None, scratch=None, fused: bool = True,
               stream=None) -> torch.Tensor:
     """h = coset-iNTT((A*B - C)/Z) with A, B, C the coset NTTs of iNTT(a|b|c)."""
@@ -190,6 +244,38 @@ def groth16_h(field, log_n: int, a, b, c, h=None, scratch=None, fused: bool = Tr
                                     _ptr(scratch), int(fused), _stream_handle(stream)),
             "zkntt_groth16_h")
     return h
+
+
+class Groth16Graph:
+    """The fused Groth16 H sequence for fixed buffers, captured once into a
+    CUDA graph and replayed with ``launch()``."""
+
+    def __init__(self, field, log_n: int, a, b, c, h, scratch, stream: torch.cuda.Stream):
+        n = 1 << log_n
+        for t in (a, b, c, h):
+            if t.numel() != 8 * n:
+                raise ValueError("vector size mismatch")
+        self._bufs = (a, b, c, h, scratch)   # keep the buffers alive with the graph
+        g = ctypes.c_void_p()
+        N.check(N.lib().zkntt_groth16_graph_create(ctypes.byref(g), _field_id(field), log_n, _ptr(a),
+                                                   _ptr(b), _ptr(c), _ptr(h), _ptr(scratch),
+                                                   _stream_handle(stream)),
+                "zkntt_groth16_graph_create")
+        self._g = g
+
+    def launch(self, stream=None):
+        N.check(N.lib().zkntt_graph_launch(self._g, _stream_handle(stream)), "zkntt_graph_launch")
+
+    def close(self):
+        if getattr(self, "_g", None) is not None:
+            N.lib().zkntt_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def field_op(field, op: str, a, b, out=None, stream=None) -> torch.Tensor:

@@ -58,7 +58,13 @@ SIGNATURES = {
     "zkntt_execute_host": [_vp, _vp, _vp, _vp],
     "zkntt_execute_noalloc": [_vp, _vp, _vp, _vp],
     "zkntt_execute_batch": [ctypes.POINTER(_vp), ctypes.POINTER(IO), _i, _vp],
+    "zkntt_execute_batch_signal": [ctypes.POINTER(_vp), ctypes.POINTER(IO), _i, _vp, ctypes.c_uint32, _vp],
+    "zkntt_flags_create": [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
+    "zkntt_flags_destroy": [_vp],
     "zkntt_groth16_h": [_i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp],
+    "zkntt_groth16_graph_create": [ctypes.POINTER(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
+    "zkntt_graph_launch": [_vp, _vp],
+    "zkntt_graph_destroy": [_vp],
     "zkntt_status_str": [_i],
     "zkntt_last_cuda_error": [ctypes.POINTER(_i)],
     "zkntt_sync_status": [_vp],

@@ -24,22 +24,27 @@ __device__ __noinline__ void batch_tile(const PassArgs &a, uint4 *smem, uint32_t
 }
 
 // ctrl[0]: next work item, ctrl[1]: abort word; done[s]: tiles retired per
-// segment; status: sticky per-device error word read by the host.
+// segment; status: sticky per-device error word read by the host.  Thread 0
+// claims the block's next work item while the current tile is processed, so
+// the atomic's round trip is hidden behind the tile.
 __global__ void __launch_bounds__(BATCH_THREADS, 2)
     batch_kernel(const __grid_constant__ BatchTable tab, uint32_t *ctrl, uint32_t *done,
                  uint32_t *status) {
     extern __shared__ uint4 smem[];
     __shared__ uint32_t s_item, s_seg, s_stop;
+    uint32_t next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(&ctrl[0], 1u);
     for (;;) {
         if (threadIdx.x == 0) {
             uint32_t stop = 0, segi = 0;
-            uint32_t item = atomicAdd(&ctrl[0], 1u);
+            const uint32_t item = next;
             if (item >= tab.total_items || *(volatile uint32_t *)&ctrl[1]) {
                 stop = 1;
             } else {
+                next = atomicAdd(&ctrl[0], 1u);  // claim ahead
                 uint32_t lo = 0, hi = tab.nseg;  // last segment with first_item <= item
                 while (hi - lo > 1) {
-                    uint32_t mid = (lo + hi) >> 1;
+                    const uint32_t mid = (lo + hi) >> 1;
                     if (tab.seg[mid].first_item <= item) lo = mid;
                     else hi = mid;
                 }
@@ -48,7 +53,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
                 for (int k = 0; k < 3 && !stop; k++) {
                     if (sg.dep[k] < 0) continue;
                     const uint32_t *cnt = done + sg.dep[k];
-                    unsigned long long t0 = global_ns();
+                    if (ld_acquire(cnt) >= sg.dep_tiles[k]) continue;
+                    const unsigned long long t0 = global_ns();
                     while (ld_acquire(cnt) < sg.dep_tiles[k]) {
                         if (*(volatile uint32_t *)&ctrl[1]) { stop = 1; break; }
                         if (global_ns() - t0 > tab.timeout_ns) {
@@ -74,7 +80,14 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
         // run_tile ends with a block barrier: every store of the tile is issued
         if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(&done[s_seg], 1u);
+            const uint32_t retired = atomicAdd(&done[s_seg], 1u) + 1u;
+            if (sg.signal && retired == sg.ntiles && tab.flags) {
+                // the transform's last tile: publish its completion to the host
+                __threadfence_system();
+                asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(tab.flags + sg.job),
+                             "r"(tab.epoch)
+                             : "memory");
+            }
         }
     }
 }

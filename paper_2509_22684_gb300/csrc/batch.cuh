@@ -36,12 +36,17 @@ struct BatchSeg {
     uint32_t first_item;  // index of the segment's first tile in the work list
     int32_t dep[3];       // segments that must be complete first (-1: none)
     uint32_t dep_tiles[3];
+    uint32_t ntiles;      // tiles in this segment
+    uint32_t job;         // index of the transform in the batch
+    uint32_t signal;      // 1: last pass of its transform and completion words requested
 };
 
 struct BatchTable {
     uint32_t nseg;
     uint32_t total_items;
     unsigned long long timeout_ns;
+    uint32_t *flags;      // per-transform completion words (may be null)
+    uint32_t epoch;       // value written to flags[job] when the job completes
     BatchSeg seg[BATCH_MAX_SEGMENTS];
 };
 

@@ -222,6 +222,7 @@ uint32_t rev_bits(uint32_t x, int bits) {
 // ---------------------------------------------------------------------------
 struct DeviceInfo {
     int sms = 0;
+    int batch_blocks_per_sm = 1;  // occupancy of the persistent batch kernel
     bool init = false;
     uint32_t *status = nullptr;  // sticky device-side error word
 };
@@ -242,6 +243,9 @@ zkntt_status device_info(DeviceInfo **out) {
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
         ZK_CHECK(cudaFuncSetAttribute(batch_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       64 * 1024));
+        ZK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.batch_blocks_per_sm, batch_kernel_ptr(),
+                                                               BATCH_THREADS, 64 * 1024));
+        d.batch_blocks_per_sm = std::max(d.batch_blocks_per_sm, 1);
         ZK_CHECK(cudaMalloc(&d.status, sizeof(uint32_t)));
         ZK_CHECK(cudaMemset(d.status, 0, sizeof(uint32_t)));
         // keep freed stream-ordered scratch in the pool between executions
@@ -674,7 +678,8 @@ struct JobSpec {
 };
 
 zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
-                          unsigned long long timeout_ns) {
+                          unsigned long long timeout_ns, uint32_t *flags = nullptr,
+                          uint32_t epoch = 0, const std::vector<uint32_t> *job_ids = nullptr) {
     DeviceInfo *dev;
     zkntt_status st = device_info(&dev);
     if (st != ZKNTT_OK) return st;
@@ -695,6 +700,8 @@ zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
     memset(tab, 0, sizeof *tab);
     tab->nseg = uint32_t(segs.size());
     tab->timeout_ns = timeout_ns;
+    tab->flags = flags;
+    tab->epoch = epoch;
     uint32_t item = 0;
     for (int k = 0; k < int(segs.size()); k++) {
         const JobSpec &J = jobs[segs[k].job];
@@ -711,6 +718,9 @@ zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
         sg.field = uint32_t(P->field);
         sg.K = uint32_t(P->ps[i].K);
         sg.first_item = item;
+        sg.ntiles = P->ps[i].num_tiles;
+        sg.job = job_ids ? (*job_ids)[segs[k].job] : uint32_t(segs[k].job);
+        sg.signal = (flags && i == P->passes - 1) ? 1u : 0u;
         item += P->ps[i].num_tiles;
         for (int d = 0; d < 3; d++) {
             sg.dep[d] = -1;
@@ -730,6 +740,14 @@ zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
                 sg.dep_tiles[d] = DP->ps[DP->passes - 1].num_tiles;
             }
         }
+        // every dependency must point to an earlier segment of the work list:
+        // that ordering is what makes the persistent schedule deadlock-free
+        for (int d = 0; d < 3; d++) {
+            if (sg.dep[d] >= k) {
+                delete tab;
+                return ZKNTT_EINVAL;
+            }
+        }
     }
     tab->total_items = item;
 
@@ -742,11 +760,8 @@ zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
     }
     e = cudaMemsetAsync(ctrl, 0, words * 4, s);
     if (e == cudaSuccess) {
-        int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel_ptr(), BATCH_THREADS,
-                                                          64 * 1024);
-        nb = std::max(nb, 1);
-        uint32_t grid = std::min<uint32_t>(item, uint32_t(nb) * dev->sms);
+        // (no occupancy query here: this path must stay legal inside a stream capture)
+        uint32_t grid = std::min<uint32_t>(item, uint32_t(dev->batch_blocks_per_sm) * dev->sms);
         uint32_t *done = ctrl + 2;
         uint32_t *status = dev->status;
         void *args[] = {tab, &ctrl, &done, &status};
@@ -767,10 +782,14 @@ unsigned long long batch_timeout_ns() {
     return ms * 1000000ull;
 }
 
-// Groth16 plans per (field, log_n): iNTT, coset NTT, coset iNTT, and the coset
-// iNTT with (g^n - 1)^-1 folded into its output scale (fused form)
+// Groth16 plans per (field, log_n).  Separate form (the sequence as stated):
+// iNTT, coset NTT, coset iNTT.  Fused form: cosetNTT_g(iNTT(a)) is computed as
+// NTT(cosetINTT_{g^-1}(a)) -- the inverse's output scale g^j then rides the
+// store of its last pass and the forward transform needs no input scale -- and
+// the final coset iNTT carries (g^n - 1)^-1 in its output scale.
 struct G16Plans {
     zkntt_plan intt = nullptr, cntt = nullptr, cintt = nullptr, cintt_z = nullptr;
+    zkntt_plan intt_gj = nullptr, ntt = nullptr;
     E8 zinv{};
 };
 std::mutex g_g16_mu;
@@ -793,8 +812,11 @@ zkntt_status g16_plans(int field, int log_n, G16Plans **out) {
         if ((s = create_plan(&G.intt, zkntt_field(field), log_n, ZKNTT_INVERSE, nullptr, &o, nullptr)) ||
             (s = create_plan(&G.cntt, zkntt_field(field), log_n, ZKNTT_FORWARD, g.data(), &o, nullptr)) ||
             (s = create_plan(&G.cintt, zkntt_field(field), log_n, ZKNTT_INVERSE, g.data(), &o, nullptr)) ||
-            (s = create_plan(&G.cintt_z, zkntt_field(field), log_n, ZKNTT_INVERSE, g.data(), &o, &G.zinv))) {
-            for (zkntt_plan *q : {&G.intt, &G.cntt, &G.cintt, &G.cintt_z})
+            (s = create_plan(&G.cintt_z, zkntt_field(field), log_n, ZKNTT_INVERSE, g.data(), &o, &G.zinv)) ||
+            (s = create_plan(&G.intt_gj, zkntt_field(field), log_n, ZKNTT_INVERSE, hinv(F, g).data(), &o,
+                             nullptr)) ||
+            (s = create_plan(&G.ntt, zkntt_field(field), log_n, ZKNTT_FORWARD, nullptr, &o, nullptr))) {
+            for (zkntt_plan *q : {&G.intt, &G.cntt, &G.cintt, &G.cintt_z, &G.intt_gj, &G.ntt})
                 if (*q) {
                     free_plan(*q);
                     *q = nullptr;
@@ -955,6 +977,76 @@ zkntt_status zkntt_execute_batch(const zkntt_plan *plans, const zkntt_io *ptrs, 
     return st;
 }
 
+zkntt_status zkntt_execute_batch_signal(const zkntt_plan *plans, const zkntt_io *ptrs, int count,
+                                        uint32_t *d_flags, uint32_t epoch, void *stream) {
+    if (count < 0 || (count > 0 && (!plans || !ptrs || !d_flags))) return ZKNTT_EINVAL;
+    if (count == 0) return ZKNTT_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    size_t scratch_total = 0;
+    for (int j = 0; j < count; j++) {
+        if (!plans[j] || bad_ptr(ptrs[j].d_in) || bad_ptr(ptrs[j].d_out)) return ZKNTT_EINVAL;
+        const size_t bytes = size_t(32) << plans[j]->log_n;
+        if (partial_overlap(ptrs[j].d_in, ptrs[j].d_out, bytes)) return ZKNTT_EINVAL;
+        scratch_total += scratch_bytes_of(plans[j]);
+    }
+    // shortest transforms first, each transform's passes back to back
+    std::vector<int> order(count);
+    for (int j = 0; j < count; j++) order[j] = j;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return plans[a]->log_n < plans[b]->log_n; });
+    char *scratch = nullptr;
+    if (scratch_total) ZK_CHECK(cudaMallocAsync(reinterpret_cast<void **>(&scratch), scratch_total, s));
+    zkntt_status st = ZKNTT_OK;
+    size_t off = 0, b = 0;
+    while (b < order.size() && st == ZKNTT_OK) {
+        std::vector<JobSpec> chunk;
+        std::vector<uint32_t> ids;
+        size_t segs = 0;
+        int level = 0;
+        while (b < order.size() && segs + plans[order[b]]->passes <= size_t(BATCH_MAX_SEGMENTS)) {
+            const int j = order[b];
+            JobSpec J;
+            J.plan = plans[j];
+            J.in = ptrs[j].d_in;
+            J.out = ptrs[j].d_out;
+            J.scratch = scratch_bytes_of(plans[j]) ? scratch + off : nullptr;
+            J.level0 = level;
+            off += scratch_bytes_of(plans[j]);
+            level += plans[j]->passes;
+            segs += plans[j]->passes;
+            chunk.push_back(J);
+            ids.push_back(uint32_t(j));
+            b++;
+        }
+        st = launch_batch(chunk, s, batch_timeout_ns(), d_flags, epoch, &ids);
+    }
+    if (scratch) {
+        zkntt_status st2 = from_cuda(cudaFreeAsync(scratch, s));
+        if (st == ZKNTT_OK) st = st2;
+    }
+    return st;
+}
+
+zkntt_status zkntt_flags_create(int count, uint32_t **host_view, uint32_t **device_view) {
+    if (count < 1 || !host_view || !device_view) return ZKNTT_EINVAL;
+    void *h = nullptr, *d = nullptr;
+    ZK_CHECK(cudaHostAlloc(&h, size_t(count) * 4, cudaHostAllocMapped));
+    memset(h, 0, size_t(count) * 4);
+    cudaError_t e = cudaHostGetDevicePointer(&d, h, 0);
+    if (e != cudaSuccess) {
+        cudaFreeHost(h);
+        return from_cuda(e);
+    }
+    *host_view = static_cast<uint32_t *>(h);
+    *device_view = static_cast<uint32_t *>(d);
+    return ZKNTT_OK;
+}
+
+zkntt_status zkntt_flags_destroy(uint32_t *host_view) {
+    if (!host_view) return ZKNTT_OK;
+    return from_cuda(cudaFreeHost(host_view));
+}
+
 zkntt_status zkntt_groth16_h(zkntt_field field, int log_n, const void *d_a, const void *d_b,
                              const void *d_c, void *d_h, void *d_scratch, int fused, void *stream) {
     if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
@@ -989,23 +1081,23 @@ zkntt_status zkntt_groth16_h(zkntt_field field, int log_n, const void *d_a, cons
         return zkntt_execute(G->cintt, d_h, d_h, s);
     }
     // fused: one persistent launch over the dependency graph
-    //   jobs 0-2: iNTT(a|b|c) -> S0|S1|S2           levels 0 .. p-1
-    //   jobs 3-5: cosetNTT in place on S0|S1|S2      levels p .. 2p-1
-    //   job 6:    cosetINTT((S0*S1 - S2)) * zinv -> h levels 2p .. 3p-1
-    const size_t per = scratch_bytes_of(G->intt);
+    //   jobs 0-2: cosetINTT_{g^-1}(a|b|c) -> S0|S1|S2   levels 0 .. p-1
+    //   jobs 3-5: NTT in place on S0|S1|S2              levels p .. 2p-1
+    //   job 6:    cosetINTT_g(S0*S1 - S2) * zinv -> h   levels 2p .. 3p-1
+    const size_t per = scratch_bytes_of(G->ntt);
     char *ps = nullptr;
     if (per) ZK_CHECK(cudaMallocAsync(reinterpret_cast<void **>(&ps), 7 * per, s));
     std::vector<JobSpec> jobs(7);
-    const int p = G->intt->passes;
+    const int p1 = G->intt_gj->passes, p2 = G->ntt->passes;
     for (int k = 0; k < 3; k++) {
-        jobs[k].plan = G->intt;
+        jobs[k].plan = G->intt_gj;
         jobs[k].in = in[k];
         jobs[k].out = sv[k];
         jobs[k].level0 = 0;
-        jobs[3 + k].plan = G->cntt;
+        jobs[3 + k].plan = G->ntt;
         jobs[3 + k].in = sv[k];
         jobs[3 + k].out = sv[k];
-        jobs[3 + k].level0 = p;
+        jobs[3 + k].level0 = p1;
         jobs[3 + k].deps[0] = k;
     }
     jobs[6].plan = G->cintt_z;
@@ -1013,7 +1105,7 @@ zkntt_status zkntt_groth16_h(zkntt_field field, int log_n, const void *d_a, cons
     jobs[6].out = d_h;
     jobs[6].pw_b = S1;
     jobs[6].pw_c = S2;
-    jobs[6].level0 = 2 * p;
+    jobs[6].level0 = p1 + p2;
     jobs[6].deps[0] = 3;
     jobs[6].deps[1] = 4;
     jobs[6].deps[2] = 5;
@@ -1024,6 +1116,59 @@ zkntt_status zkntt_groth16_h(zkntt_field field, int log_n, const void *d_a, cons
         if (st == ZKNTT_OK) st = st2;
     }
     return st;
+}
+
+struct zkntt_graph_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+zkntt_status zkntt_groth16_graph_create(zkntt_graph *out, zkntt_field field, int log_n,
+                                        const void *d_a, const void *d_b, const void *d_c, void *d_h,
+                                        void *d_scratch, void *stream) {
+    if (!out) return ZKNTT_EINVAL;
+    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (log_n < 1 || log_n > 28) return ZKNTT_EINVAL;
+    if (!stream) return ZKNTT_EINVAL;  // the legacy default stream cannot be captured
+    // everything that allocates or synchronises happens before the capture
+    G16Plans *G;
+    zkntt_status st = g16_plans(field, log_n, &G);
+    if (st != ZKNTT_OK) return st;
+    DeviceInfo *dev;
+    st = device_info(&dev);
+    if (st != ZKNTT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    zkntt_graph_s *g = new (std::nothrow) zkntt_graph_s;
+    if (!g) return ZKNTT_ENOMEM;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        delete g;
+        return from_cuda(e);
+    }
+    st = zkntt_groth16_h(field, log_n, d_a, d_b, d_c, d_h, d_scratch, 1, stream);
+    e = cudaStreamEndCapture(s, &g->graph);
+    if (st == ZKNTT_OK && e == cudaSuccess)
+        e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (st != ZKNTT_OK || e != cudaSuccess) {
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return st != ZKNTT_OK ? st : from_cuda(e);
+    }
+    *out = g;
+    return ZKNTT_OK;
+}
+
+zkntt_status zkntt_graph_launch(zkntt_graph graph, void *stream) {
+    if (!graph || !graph->exec) return ZKNTT_EINVAL;
+    return from_cuda(cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)));
+}
+
+zkntt_status zkntt_graph_destroy(zkntt_graph graph) {
+    if (!graph) return ZKNTT_OK;
+    if (graph->exec) cudaGraphExecDestroy(graph->exec);
+    if (graph->graph) cudaGraphDestroy(graph->graph);
+    delete graph;
+    return ZKNTT_OK;
 }
 
 const char *zkntt_status_str(zkntt_status status) {

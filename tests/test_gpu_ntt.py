@@ -164,3 +164,17 @@ def test_interleaved_butterflies(F, kind, digits, cols):
     got = to_host(y)
     want = _oracle(F, X, kind)
     assert np.array_equal(got, want), first_mismatch(got, want)
+
+
+def test_tuner_picks_a_schedule_that_stays_exact(tmp_path, monkeypatch):
+    import paper_2509_22684_gb300 as zk
+    monkeypatch.setenv("ZKNTT_TUNE_CACHE", str(tmp_path / "tune.jsonl"))
+    F = fld.BN254
+    L = 17
+    best = zk.tune(F.name, L, inverse=True, max_candidates=6)
+    assert sum(best["digits"]) == L and best["ms"] > 0
+    X, x = rand_dev(F, L, 1717)
+    with zk.Plan(F.name, L, inverse=True, use_tuner=True) as p:
+        assert p.describe()["digits"] == best["digits"]
+        got = to_host(p.execute(x))
+    assert np.array_equal(got, cpu.ntt(F, X, inverse=True))
