@@ -381,18 +381,35 @@ def run_ours(args, world, rank, local):
     ms_max = max_over_ranks(world, ms_total)
     zk.sync_status(stream)
 
-    # end to end through the host-buffer entry point: pinned host input,
-    # H2D + transform + D2H inside the timed region
+    # end to end through the host-buffer entry point (zkntt_execute_host):
+    # pinned host input and output, H2D + transform + D2H inside the timed
+    # region for every step.  Steps rotate over three streams, so one step's
+    # copies overlap another step's transform (the link is full duplex).
+    nstreams = 3
+    e2e_streams = [torch.cuda.Stream() for _ in range(nstreams)]
     xh = torch.from_numpy(X.view(np.int32)).pin_memory()
-    yh = torch.empty_like(xh).pin_memory()
-    e2e_step = lambda: plan.execute_host(xh, yh, stream=stream)
-    for _ in range(max(1, min(args.warmup, 3))):
-        e2e_step()
-    torch.cuda.synchronize()
+    yhs = [torch.empty_like(xh).pin_memory() for _ in range(nstreams)]
+    k = [0]
+
+    def e2e_step():
+        i = k[0] % nstreams
+        k[0] += 1
+        plan.execute_host(xh, yhs[i], stream=e2e_streams[i])
+
+    def e2e_run(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3
+
+    e2e_run(max(3, min(args.warmup, 6)))
     barrier(world)
-    e2e_steps = max(1, min(args.steps, 10))
-    ms_e2e = max_over_ranks(world, timed(e2e_step, stream, e2e_steps))
-    ok = bool(np.array_equal(yh.numpy().view(np.uint32), y.cpu().numpy().view(np.uint32)))
+    e2e_steps = max(6, min(args.steps, 12))
+    ms_e2e = max_over_ranks(world, e2e_run(e2e_steps))
+    ok = all(bool(np.array_equal(yh.numpy().view(np.uint32), y.cpu().numpy().view(np.uint32)))
+             for yh in yhs)
 
     passes = desc["passes"]
     avg_launch_s = ms_total / 1e3 / (args.steps * passes)
@@ -429,7 +446,9 @@ def run_ours(args, world, rank, local):
                      "hbm_peak_gbs": hbm_gbs},
         "e2e": {"value": round(world * n * e2e_steps / (ms_e2e / 1e3) / 1e6, 2), "unit": "Melem/s",
                 "h2d_bytes_per_step": 32 * n, "d2h_bytes_per_step": 32 * n,
-                "api": "zkntt_execute_host (pinned host buffers)", "matches_device_result": ok},
+                "api": "zkntt_execute_host (pinned host buffers, steps over 3 streams)",
+                "timing": "host wall clock around the steps with device synchronisation on both sides",
+                "matches_device_result": ok},
         "gpu_launches": args.steps * passes,
         "clocks": clk,
     }

@@ -68,7 +68,9 @@ typedef struct {
     int num_passes;        /* 0 = planner's choice; else 1..4 */
     int digit_bits[4];     /* log2 sub-transform size per pass, top digit first; sum = log_n */
     int cols_per_cta[4];   /* columns per thread block per pass (1,2,4,8); 0 = planner's choice */
-    int use_tuner;         /* 1 = consult the tuning cache (ZKNTT_TUNE_CACHE) */
+    int use_tuner;         /* 0 or 1: use a tuned schedule when one is known for this GPU
+                              (zkntt_tuned.jsonl beside the library, then ZKNTT_TUNE_CACHE);
+                              -1: never (planner heuristic only) */
     int ilp;               /* butterflies each thread interleaves per stage step: 1 or 2; 0 = auto */
 } zkntt_plan_options;
 
@@ -272,7 +274,9 @@ typedef struct {
  * mode) for one plain transform of 2^log_n elements on the current device with
  * CUDA events, remember the fastest for this GPU (and append it to the file
  * named by ZKNTT_TUNE_CACHE, one JSON object per line) and return it in *best
- * (may be NULL).  Plans created with opts->use_tuner = 1 then use it.  Uses
+ * (may be NULL).  Plans created afterwards use it (unless opts->use_tuner < 0
+ * or the caller forces a digit split).  Schedules tuned ahead of time ship in
+ * zkntt_tuned.jsonl beside the library.  Uses
  * 3 * n * 32 bytes of temporary device memory; synchronous.
  */
 zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_candidates,

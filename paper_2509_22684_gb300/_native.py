@@ -10,7 +10,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libzkntt.so")
+# ZKNTT_LIB selects another build of the library (variants built with ZKNTT_LIB_OUT)
+LIB_PATH = os.environ.get("ZKNTT_LIB") or os.path.join(HERE, "libzkntt.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
 FIELDS = {"bls12_381_fr": 0, "bn254_fr": 1}

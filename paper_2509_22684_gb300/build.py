@@ -14,8 +14,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
-OBJ = os.path.join(HERE, "_build")
-LIB = os.path.join(HERE, "libzkntt.so")
+# ZKNTT_NVCC_FLAGS adds compile flags (e.g. -DZKNTT_MUL_FORM=1) and
+# ZKNTT_LIB_OUT names another output library, for building variants side by side
+EXTRA = os.environ.get("ZKNTT_NVCC_FLAGS", "").split()
+LIB = os.environ.get("ZKNTT_LIB_OUT") or os.path.join(HERE, "libzkntt.so")
+OBJ = os.path.join(HERE, "_build") if LIB == os.path.join(HERE, "libzkntt.so") else LIB + ".objs"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}",
@@ -39,7 +42,7 @@ def _compile(unit: str, hdr_mtime: float, verbose: bool) -> str:
     obj = os.path.join(OBJ, unit.replace(".cu", ".o"))
     if os.path.exists(obj) and os.path.getmtime(obj) > max(os.path.getmtime(src), hdr_mtime):
         return obj
-    cmd = [_nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj + ".tmp"]
+    cmd = [_nvcc(), *ARCH, *FLAGS, *EXTRA, "-c", src, "-o", obj + ".tmp"]
     if verbose:
         print(" ".join(cmd), flush=True)
     res = subprocess.run(cmd, capture_output=True, text=True)

@@ -164,6 +164,31 @@ __device__ __forceinline__ void merge_product_row(uint32_t t[9], const uint64_t 
           "r"(hi[6]), "r"(hi[7]));
 }
 
+// addend-form product merge: with P_j = a_j b_i + t_j,
+// t = P_0.lo, P_0.hi + P_1.lo, ..., P_6.hi + P_7.lo, P_7.hi + t_8
+__device__ __forceinline__ void merge_addend_row(uint32_t t[9], const uint64_t P[8]) {
+    uint32_t lo[8], hi[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        lo[j] = uint32_t(P[j]);
+        hi[j] = uint32_t(P[j] >> 32);
+    }
+    t[0] = lo[0];
+    asm("add.cc.u32  %0, %8, %16;\n\t"
+        "addc.cc.u32 %1, %9, %17;\n\t"
+        "addc.cc.u32 %2, %10, %18;\n\t"
+        "addc.cc.u32 %3, %11, %19;\n\t"
+        "addc.cc.u32 %4, %12, %20;\n\t"
+        "addc.cc.u32 %5, %13, %21;\n\t"
+        "addc.cc.u32 %6, %14, %22;\n\t"
+        "addc.u32    %7, %15, %7;"
+        : "=r"(t[1]), "=r"(t[2]), "=r"(t[3]), "=r"(t[4]), "=r"(t[5]), "=r"(t[6]), "=r"(t[7]),
+          "+r"(t[8])
+        : "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]),
+          "r"(hi[7]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]),
+          "r"(lo[7]));
+}
+
 // reduction merge: t'_j = Q_j.hi + Q_{j+1}.lo (j < 7), t'_7 = Q_7.hi + t_8
 __device__ __forceinline__ void merge_reduce(uint32_t t[9], const uint64_t Q[8]) {
     uint32_t lo[8], hi[8];
@@ -189,6 +214,14 @@ __device__ __forceinline__ void merge_reduce(uint32_t t[9], const uint64_t Q[8])
     t[8] = 0;
 }
 
+// Product-row / reduction-row forms (build-time choice, see the comment above):
+//   0: product rows without addend, reduction rows with the 64-bit addend
+//   1: neither row uses the addend (all merging on the ALU pipe)
+//   2: both rows use the addend
+#ifndef ZKNTT_MUL_FORM
+#define ZKNTT_MUL_FORM 0
+#endif
+
 // r = a * b * 2^-256 mod p; a, b canonical; r may alias a or b
 template <class F>
 __device__ __forceinline__ void mul(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
@@ -200,15 +233,30 @@ __device__ __forceinline__ void mul(uint32_t r[8], const uint32_t a[8], const ui
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         uint64_t X[8];
+        if (ZKNTT_MUL_FORM == 2) {
 #pragma unroll
-        for (int j = 0; j < 8; j++) X[j] = uint64_t(a[j]) * bb[i];
-        merge_product_row(t, X);
+            for (int j = 0; j < 8; j++) X[j] = uint64_t(a[j]) * bb[i] + t[j];
+            merge_addend_row(t, X);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; j++) X[j] = uint64_t(a[j]) * bb[i];
+            merge_product_row(t, X);
+        }
         // m = t_0 r' mod 2^32 (for BLS12-381 F_r, r' = 2^32 - 1 and r_0 = 1,
         // r_1 = 2^32 - 1: the compiler turns those products into adds)
         const uint32_t m = t[0] * F::RP;
+        if (ZKNTT_MUL_FORM == 1) {
 #pragma unroll
-        for (int j = 0; j < 8; j++) X[j] = uint64_t(m) * P[j] + t[j];
-        merge_reduce(t, X);
+            for (int j = 0; j < 8; j++) X[j] = uint64_t(m) * P[j];
+            merge_product_row(t, X);  // t_0 becomes 0: shift down one limb
+#pragma unroll
+            for (int j = 0; j < 8; j++) t[j] = t[j + 1];
+            t[8] = 0;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; j++) X[j] = uint64_t(m) * P[j] + t[j];
+            merge_reduce(t, X);
+        }
     }
     reduce_once<F>(t);
 #pragma unroll

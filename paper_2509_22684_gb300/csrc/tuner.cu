@@ -1,6 +1,7 @@
 // tuner.cu -- the autotuner: search over pass splits, block shapes and twiddle
 // modes for one transform size, timed on the device with CUDA events.
 #include <cuda_runtime.h>
+#include <dlfcn.h>
 
 #include <algorithm>
 #include <cstdio>
@@ -42,13 +43,29 @@ const char *cache_path() {
     return (p && *p) ? p : nullptr;
 }
 
+// schedules shipped with the library: "zkntt_tuned.jsonl" in the directory of
+// the shared library itself (same format as the user cache)
+std::string bundled_path() {
+    Dl_info info;
+    if (dladdr(reinterpret_cast<void *>(&tuner_lookup), &info) == 0 || !info.dli_fname) return "";
+    std::string so = info.dli_fname;
+    size_t slash = so.rfind('/');
+    return (slash == std::string::npos ? std::string(".") : so.substr(0, slash)) + "/zkntt_tuned.jsonl";
+}
+
 // one entry per line:
 // {"gpu":"NAME","field":F,"log_n":L,"dir":D,"passes":P,"digits":[a,b,c,d],"log_cols":[a,b,c,d],"mode":M,"ilp":I,"ms":T}
+void load_file(const char *path);
+
 void load_locked() {
     if (g_loaded) return;
     g_loaded = true;
-    const char *path = cache_path();
-    if (!path) return;
+    const std::string b = bundled_path();
+    if (!b.empty()) load_file(b.c_str());
+    if (const char *path = cache_path()) load_file(path);  // user entries override
+}
+
+void load_file(const char *path) {
     FILE *f = fopen(path, "r");
     if (!f) return;
     char line[1024];

@@ -398,7 +398,10 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
     int mode = ZKNTT_TWIDDLE_AUTO;
     int ilp = DEFAULT_ILP;
     default_digits(L, &P->passes, k);
-    if (opts && opts->use_tuner) {
+    // tuned schedules (shipped with the library or from ZKNTT_TUNE_CACHE) are
+    // used unless the caller opts out (use_tuner < 0) or forces a split
+    const bool explicit_split = opts && opts->num_passes > 0;
+    if (!explicit_split && !(opts && opts->use_tuner < 0)) {
         TuneEntry te;
         if (tuner_lookup(P->field, L, P->dir, &te)) {
             P->passes = te.passes;
@@ -452,6 +455,9 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
         const bool last = (i == p - 1);
         const int span = last ? ps.hi_bits : ps.lo_bits;
         int lc = default_log_cols(ps.K, span);
+        // keep at least four tiles per SM so the persistent grid fills the GPU
+        while (lc > 0 && ((L - ps.K - lc) < 0 || (uint64_t(1) << (L - ps.K - lc)) < uint64_t(4) * dev->sms))
+            lc--;
         if (opts && opts->cols_per_cta[i] > 0) {
             int c = opts->cols_per_cta[i], l = 0;
             while ((1 << l) < c) l++;
