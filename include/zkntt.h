@@ -71,7 +71,10 @@ typedef struct {
     int use_tuner;         /* 0 or 1: use a tuned schedule when one is known for this GPU
                               (zkntt_tuned.jsonl beside the library, then ZKNTT_TUNE_CACHE);
                               -1: never (planner heuristic only) */
-    int ilp;               /* butterflies each thread interleaves per stage step: 1 or 2; 0 = auto */
+    int ilp;               /* kernel variant: 1 = one butterfly per thread per stage step (3 blocks
+                              per SM), 2 = two interleaved butterflies (2 blocks), 3 = one
+                              butterfly with registers for 4 blocks, 4 = software-pipelined
+                              stage loop (2 blocks); 0 = auto */
 } zkntt_plan_options;
 
 /*

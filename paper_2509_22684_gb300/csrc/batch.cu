@@ -27,7 +27,7 @@ __device__ __noinline__ void batch_tile(const PassArgs &a, uint4 *smem, uint32_t
 // segment; status: sticky per-device error word read by the host.  Thread 0
 // claims the block's next work item while the current tile is processed, so
 // the atomic's round trip is hidden behind the tile.
-__global__ void __launch_bounds__(BATCH_THREADS, 2)
+__global__ void __launch_bounds__(BATCH_THREADS, BATCH_MIN_BLOCKS)
     batch_kernel(const __grid_constant__ BatchTable tab, uint32_t *ctrl, uint32_t *done,
                  uint32_t *status) {
     extern __shared__ uint4 smem[];

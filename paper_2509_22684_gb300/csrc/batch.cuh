@@ -27,6 +27,8 @@ namespace zkntt {
 
 constexpr int BATCH_MAX_SEGMENTS = 160;
 constexpr uint32_t BATCH_THREADS = 256;
+// blocks per SM the register budget is compiled for (80 registers a thread)
+constexpr int BATCH_MIN_BLOCKS = 3;
 constexpr uint32_t BATCH_STATUS_TIMEOUT = 4u;  // == ZKNTT_ETIMEOUT
 
 struct BatchSeg {

@@ -9,7 +9,7 @@ constexpr int MAX_DIGIT_BITS = 11;  // largest sub-transform a block holds (2^11
 constexpr int MAX_TILE_BITS = 11;   // tiles hold at most 2^11 elements (C x 2^K)
 
 struct FieldKernels {
-    const void *pass[3];  // ntt_pass_kernel<F, ILP> at index ILP = 1, 2 (digit size is a runtime argument)
+    const void *pass[5];  // ntt_pass_kernel<F, V> at index V = 1..4 (digit size is a runtime argument)
     const void *gen_powers;
     const void *gen_twiddle;
     const void *field_op;

@@ -215,10 +215,49 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
         const uint32_t lh = K - 1 - s;
         const uint32_t h = 1u << lh;
         const uint4 *ws = a.w_stage + 2 * size_t(N - 2 * h);
-        for (uint32_t bg = tid; active && bg < (CN >> 1); bg += ILP * nthreads) {
-            uint32_t x[ILP][8], y[ILP][8], w[ILP][8], t[ILP][8], s0[ILP], s1[ILP];
+        if constexpr (ILP == 0) {
+            // software-pipelined: the product of one butterfly overlaps the
+            // loads and add/subtract of the next (every thread owns >= 2)
+            uint32_t x[8], t[8], w[8], s0, s1;
+            auto prepare = [&](uint32_t bk, uint32_t px[8], uint32_t pt[8], uint32_t pw[8],
+                               uint32_t &q0, uint32_t &q1) {
+                const uint32_t cc = bk >> (K - 1);
+                const uint32_t b = bk & ((N >> 1) - 1);
+                const uint32_t j = b & (h - 1);
+                const uint32_t i0 = ((b >> lh) << (lh + 1)) | j;
+                q0 = smem_slot(cc, i0, K, lc);
+                q1 = smem_slot(cc, i0 + h, K, lc);
+                uint32_t py[8];
+                lds_elem(px, s_lo, s_hi, q0);
+                lds_elem(py, s_lo, s_hi, q1);
+                ldg_elem(pw, ws + 2 * size_t(j));
+                sub<F>(pt, px, py);
+                add<F>(px, px, py);
+            };
+            if (active) prepare(tid, x, t, w, s0, s1);
+            for (uint32_t bg = tid; active && bg < (CN >> 1); bg += nthreads) {
+                const uint32_t nb = bg + nthreads;
+                uint32_t x2[8], t2[8], w2[8], n0 = 0, n1 = 0;
+                if (nb < (CN >> 1)) prepare(nb, x2, t2, w2, n0, n1);
+                uint32_t y[8];
+                mul<F>(y, t, w);
+                sts_elem(s_lo, s_hi, s0, x);
+                sts_elem(s_lo, s_hi, s1, y);
 #pragma unroll
-            for (int k = 0; k < ILP; k++) {
+                for (int k = 0; k < 8; k++) {
+                    x[k] = x2[k];
+                    t[k] = t2[k];
+                    w[k] = w2[k];
+                }
+                s0 = n0;
+                s1 = n1;
+            }
+        } else {
+        for (uint32_t bg = tid; active && bg < (CN >> 1); bg += ILP * nthreads) {
+            constexpr int IL = ILP > 0 ? ILP : 1;
+            uint32_t x[IL][8], y[IL][8], w[IL][8], t[IL][8], s0[IL], s1[IL];
+#pragma unroll
+            for (int k = 0; k < IL; k++) {
                 const uint32_t bk = bg + k * nthreads;
                 const uint32_t cc = bk >> (K - 1);
                 const uint32_t b = bk & ((N >> 1) - 1);
@@ -231,17 +270,18 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
                 ldg_elem(w[k], ws + 2 * size_t(j));
             }
 #pragma unroll
-            for (int k = 0; k < ILP; k++) {
+            for (int k = 0; k < IL; k++) {
                 sub<F>(t[k], x[k], y[k]);
                 add<F>(x[k], x[k], y[k]);
             }
 #pragma unroll
-            for (int k = 0; k < ILP; k++) mul<F>(y[k], t[k], w[k]);
+            for (int k = 0; k < IL; k++) mul<F>(y[k], t[k], w[k]);
 #pragma unroll
-            for (int k = 0; k < ILP; k++) {
+            for (int k = 0; k < IL; k++) {
                 sts_elem(s_lo, s_hi, s0[k], x[k]);
                 sts_elem(s_lo, s_hi, s1[k], y[k]);
             }
+        }
         }
         __syncthreads();
     }
@@ -314,13 +354,24 @@ __host__ __device__ constexpr uint32_t pass_threads(uint32_t K, uint32_t lc) {
                : 256u;
 }
 
-// ILP = independent butterflies per thread per stage step (1 or 2); the
-// register budget follows: 3 blocks of 256 threads per SM for 1, 2 for 2.
-template <class F, int ILP>
-__global__ void __launch_bounds__(256, ILP == 1 ? 3 : 2) ntt_pass_kernel(const PassArgs a) {
+// Schedule variants (the plan's `ilp` option):
+//   1: one butterfly per thread per stage step, registers for 3 blocks of 256
+//   2: two interleaved butterflies per thread, registers for 2 blocks
+//   3: one butterfly per thread, registers for 4 blocks (tiles of <= 1024
+//      elements so four fit in shared memory)
+//   4: software-pipelined stage loop (the product of one butterfly overlaps
+//      the loads and add/subtract of the next), registers for 2 blocks
+template <int V> struct PassVariant;
+template <> struct PassVariant<1> { static constexpr int ILP = 1, MIN_BLOCKS = 3; };
+template <> struct PassVariant<2> { static constexpr int ILP = 2, MIN_BLOCKS = 2; };
+template <> struct PassVariant<3> { static constexpr int ILP = 1, MIN_BLOCKS = 4; };
+template <> struct PassVariant<4> { static constexpr int ILP = 0, MIN_BLOCKS = 2; };  // pipelined
+
+template <class F, int V>
+__global__ void __launch_bounds__(256, PassVariant<V>::MIN_BLOCKS) ntt_pass_kernel(const PassArgs a) {
     extern __shared__ uint4 smem[];
     for (uint32_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x)
-        run_tile<F, ILP>(a, smem, tile, blockDim.x);
+        run_tile<F, PassVariant<V>::ILP>(a, smem, tile, blockDim.x);
 }
 
 }  // namespace zkntt

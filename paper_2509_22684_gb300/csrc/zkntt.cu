@@ -222,7 +222,8 @@ uint32_t rev_bits(uint32_t x, int bits) {
 // ---------------------------------------------------------------------------
 struct DeviceInfo {
     int sms = 0;
-    int batch_blocks_per_sm = 1;  // occupancy of the persistent batch kernel
+    int batch_blocks_per_sm[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // batch kernel occupancy for
+                                                            // 2^(10+i) bytes of smem
     bool init = false;
     uint32_t *status = nullptr;  // sticky device-side error word
 };
@@ -238,14 +239,16 @@ zkntt_status device_info(DeviceInfo **out) {
     if (!d.init) {
         ZK_CHECK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
         for (int f = 0; f < 2; f++)
-            for (int ilp = 1; ilp <= 2; ilp++)
+            for (int ilp = 1; ilp <= 4; ilp++)
                 ZK_CHECK(cudaFuncSetAttribute(field_kernels(f).pass[ilp],
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
         ZK_CHECK(cudaFuncSetAttribute(batch_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       64 * 1024));
-        ZK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.batch_blocks_per_sm, batch_kernel_ptr(),
-                                                               BATCH_THREADS, 64 * 1024));
-        d.batch_blocks_per_sm = std::max(d.batch_blocks_per_sm, 1);
+        for (int i = 0; i < 7; i++) {
+            ZK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &d.batch_blocks_per_sm[i], batch_kernel_ptr(), BATCH_THREADS, size_t(1024) << i));
+            d.batch_blocks_per_sm[i] = std::max(d.batch_blocks_per_sm[i], 1);
+        }
         ZK_CHECK(cudaMalloc(&d.status, sizeof(uint32_t)));
         ZK_CHECK(cudaMemset(d.status, 0, sizeof(uint32_t)));
         // keep freed stream-ordered scratch in the pool between executions
@@ -410,7 +413,7 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
                 cols[i] = te.log_cols[i];
             }
             mode = te.mode;
-            if (te.ilp == 1 || te.ilp == 2) ilp = te.ilp;
+            if (te.ilp >= 1 && te.ilp <= 4) ilp = te.ilp;
         }
     }
     if (opts && opts->num_passes > 0) {
@@ -429,7 +432,7 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
     }
     if (opts && opts->twiddle_mode) mode = opts->twiddle_mode;
     if (opts && opts->ilp) {
-        if (opts->ilp != 1 && opts->ilp != 2) return ZKNTT_EINVAL;
+        if (opts->ilp < 1 || opts->ilp > 4) return ZKNTT_EINVAL;
         ilp = opts->ilp;
     }
     if (mode != ZKNTT_TWIDDLE_OTF) mode = ZKNTT_TWIDDLE_PRECOMP;
@@ -700,6 +703,22 @@ zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
     if (segs.size() > size_t(BATCH_MAX_SEGMENTS)) return ZKNTT_EUNSUPPORTED;
     std::map<std::pair<int, int>, int> index;
     for (int k = 0; k < int(segs.size()); k++) index[{segs[k].job, segs[k].pass}] = k;
+    // The batch kernel runs 256 threads a block whatever the tile, so a tile of
+    // C x 2^K elements with C x 2^K / 4 < 256 leaves threads idle.  Each pass
+    // therefore takes the widest tile its digit allows, narrowed toward the
+    // plan's own width only while the pass has fewer tiles than one wave of
+    // resident blocks (the plan's tables do not depend on the tile width).
+    const uint64_t wave = uint64_t(dev->sms) * BATCH_MIN_BLOCKS;
+    auto batch_log_cols = [&](const zkntt_plan_s *P, int i) {
+        const PassPlan &ps = P->ps[i];
+        const int span = (i == P->passes - 1) ? ps.hi_bits : ps.lo_bits;
+        int lc = std::max(0, std::min({3, MAX_TILE_BITS - ps.K, span}));
+        while (lc > ps.log_cols && (uint64_t(1) << (P->log_n - ps.K - lc)) < wave) lc--;
+        return lc;
+    };
+    auto batch_tiles = [&](const zkntt_plan_s *P, int i) {
+        return uint32_t(1) << (P->log_n - P->ps[i].K - batch_log_cols(P, i));
+    };
 
     BatchTable *tab = new (std::nothrow) BatchTable;
     if (!tab) return ZKNTT_ENOMEM;
@@ -717,6 +736,8 @@ zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
         void *dst = (i == P->passes - 1) ? J.out : J.scratch;
         BatchSeg &sg = tab->seg[k];
         sg.a = pass_args(P, i, src, dst);
+        sg.a.log_cols = uint32_t(batch_log_cols(P, i));
+        sg.a.num_tiles = batch_tiles(P, i);
         if (i == 0) {
             sg.a.pw_b = static_cast<const uint4 *>(J.pw_b);
             sg.a.pw_c = static_cast<const uint4 *>(J.pw_c);
@@ -724,10 +745,10 @@ zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
         sg.field = uint32_t(P->field);
         sg.K = uint32_t(P->ps[i].K);
         sg.first_item = item;
-        sg.ntiles = P->ps[i].num_tiles;
+        sg.ntiles = sg.a.num_tiles;
         sg.job = job_ids ? (*job_ids)[segs[k].job] : uint32_t(segs[k].job);
         sg.signal = (flags && i == P->passes - 1) ? 1u : 0u;
-        item += P->ps[i].num_tiles;
+        item += sg.a.num_tiles;
         for (int d = 0; d < 3; d++) {
             sg.dep[d] = -1;
             sg.dep_tiles[d] = 0;
@@ -735,7 +756,7 @@ zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
         if (i > 0) {
             int dk = index[{segs[k].job, i - 1}];
             sg.dep[0] = dk;
-            sg.dep_tiles[0] = jobs[segs[k].job].plan->ps[i - 1].num_tiles;
+            sg.dep_tiles[0] = batch_tiles(jobs[segs[k].job].plan, i - 1);
         } else {
             for (int d = 0; d < 3; d++) {
                 int dj = J.deps[d];
@@ -743,7 +764,7 @@ zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
                 const zkntt_plan_s *DP = jobs[dj].plan;
                 int dk = index[{dj, DP->passes - 1}];
                 sg.dep[d] = dk;
-                sg.dep_tiles[d] = DP->ps[DP->passes - 1].num_tiles;
+                sg.dep_tiles[d] = batch_tiles(DP, DP->passes - 1);
             }
         }
         // every dependency must point to an earlier segment of the work list:
@@ -766,14 +787,21 @@ zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
     }
     e = cudaMemsetAsync(ctrl, 0, words * 4, s);
     if (e == cudaSuccess) {
-        // (no occupancy query here: this path must stay legal inside a stream capture)
-        uint32_t grid = std::min<uint32_t>(item, uint32_t(dev->batch_blocks_per_sm) * dev->sms);
+        // shared memory for the largest tile of the launch; occupancy comes from
+        // the table built at device set-up (no query here: this path must stay
+        // legal inside a stream capture)
+        size_t smem = 1024;
+        for (int k = 0; k < int(segs.size()); k++)
+            smem = std::max(smem, size_t(32) << (tab->seg[k].a.K + tab->seg[k].a.log_cols));
+        int si = 0;
+        while ((size_t(1024) << si) < smem) si++;
+        smem = size_t(1024) << si;
+        uint32_t grid = std::min<uint32_t>(item, uint32_t(dev->batch_blocks_per_sm[si]) * dev->sms);
         uint32_t *done = ctrl + 2;
         uint32_t *status = dev->status;
         void *args[] = {tab, &ctrl, &done, &status};
         if (e == cudaSuccess && grid > 0)
-            e = cudaLaunchKernel(batch_kernel_ptr(), dim3(grid), dim3(BATCH_THREADS), args,
-                                 64 * 1024, s);
+            e = cudaLaunchKernel(batch_kernel_ptr(), dim3(grid), dim3(BATCH_THREADS), args, smem, s);
     }
     cudaError_t e2 = cudaFreeAsync(ctrl, s);
     delete tab;
