@@ -250,8 +250,12 @@ zkntt_status zkntt_field_info(zkntt_field field, uint32_t modulus[8], uint32_t g
 
 /* Elementwise field operations on device vectors of n elements (test and
  * calibration entry points for the butterfly arithmetic):
- *   op 0: c = a * b (Montgomery product a b 2^-256 mod r)
+ *   op 0: c = a * b (Montgomery product a b 2^-256 mod r, canonical; a must be
+ *         canonical, b may be any 256-bit value)
  *   op 1: c = a + b mod r      op 2: c = a - b mod r
+ *   op 3: c = a + r - b, the unreduced butterfly difference (in (0, 2r) for
+ *         canonical a, b; it feeds the product as its second operand)
+ * Inputs of ops 1-3 must be canonical.  op outside 0..3 -> ZKNTT_EINVAL.
  */
 zkntt_status zkntt_field_op(zkntt_field field, int op, const void *d_a, const void *d_b, void *d_c,
                             size_t n, void *stream);

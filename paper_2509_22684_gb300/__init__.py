@@ -279,7 +279,7 @@ class Groth16Graph:
 
 
 def field_op(field, op: str, a, b, out=None, stream=None) -> torch.Tensor:
-    ops = {"mul": 0, "add": 1, "sub": 2}
+    ops = {"mul": 0, "add": 1, "sub": 2, "sub_lazy": 3}
     out = torch.empty_like(a) if out is None else out
     N.check(N.lib().zkntt_field_op(_field_id(field), ops[op], _ptr(a), _ptr(b), _ptr(out),
                                    a.numel() // 8, _stream_handle(stream)), "zkntt_field_op")

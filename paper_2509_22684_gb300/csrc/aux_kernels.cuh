@@ -63,7 +63,8 @@ __global__ void field_op_kernel(int op, const uint4 *a, const uint4 *b, uint4 *c
         ldg_elem(y, b + 2 * i);
         if (op == 0) mul<F>(z, x, y);
         else if (op == 1) add<F>(z, x, y);
-        else sub<F>(z, x, y);
+        else if (op == 2) sub<F>(z, x, y);
+        else sub_lazy<F>(z, x, y);
         st_elem(c + 2 * i, z);
     }
 }

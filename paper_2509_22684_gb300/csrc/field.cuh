@@ -114,6 +114,36 @@ __device__ __forceinline__ void sub(uint32_t r[8], const uint32_t a[8], const ui
           "r"(F::P4 & mask), "r"(F::P5 & mask), "r"(F::P6 & mask), "r"(F::P7 & mask));
 }
 
+// r = a + p - b, in (0, 2p) and congruent to a - b, for canonical a, b: no
+// conditional correction.  Only for values that feed mul as its second
+// (limb-scanned) operand, which may be any value below 2^256.
+template <class F>
+__device__ __forceinline__ void sub_lazy(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) r[i] = a[i];
+    asm("add.cc.u32  %0, %0, %16;\n\t"
+        "addc.cc.u32 %1, %1, %17;\n\t"
+        "addc.cc.u32 %2, %2, %18;\n\t"
+        "addc.cc.u32 %3, %3, %19;\n\t"
+        "addc.cc.u32 %4, %4, %20;\n\t"
+        "addc.cc.u32 %5, %5, %21;\n\t"
+        "addc.cc.u32 %6, %6, %22;\n\t"
+        "addc.u32    %7, %7, %23;\n\t"
+        "sub.cc.u32  %0, %0, %8;\n\t"
+        "subc.cc.u32 %1, %1, %9;\n\t"
+        "subc.cc.u32 %2, %2, %10;\n\t"
+        "subc.cc.u32 %3, %3, %11;\n\t"
+        "subc.cc.u32 %4, %4, %12;\n\t"
+        "subc.cc.u32 %5, %5, %13;\n\t"
+        "subc.cc.u32 %6, %6, %14;\n\t"
+        "subc.u32    %7, %7, %15;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+          "+r"(r[7])
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]),
+          "n"(F::P0), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5), "n"(F::P6),
+          "n"(F::P7));
+}
+
 // ---------------------------------------------------------------------------
 // Montgomery product, CIOS with one 64-bit partial product per limb pair.
 //
@@ -128,11 +158,14 @@ __device__ __forceinline__ void sub(uint32_t r[8], const uint32_t a[8], const ui
 // Why this split: on GB300 the wide multiplies run on the heavy FMA datapath
 // at half rate, and a multiply-add whose 64-bit addend is a zero-extended
 // 32-bit value also needs a move on that datapath, while the add chains run on
-// the ALU pipe.  Using the addend form only in the reduction rows balances the
-// two pipes: about 405 instructions and 600 heavy-pipe cycles per warp-wide
-// product, against 576 instructions for separate mad.lo.cc / madc.hi.cc
-// chains (measured: 53 vs 43 G products/s for BLS12-381 F_r).  With r < 2^255
-// (both fields) t < 2r holds after every step, so t_8 never carries out.
+// the ALU pipe.  Using the addend form in the reduction rows and in the last
+// product row, and plain wide products with two add chains in the others,
+// balances the two pipes.  The first product row starts from t = 0, and the
+// asm chains are opaque to the compiler, so it gets its own single chain
+// instead of adding zeros.  Measured on GB300, BLS12-381 F_r: 58.3 G
+// products/s, against 55.7 with every product row in the two-chain form and
+// 43 for separate mad.lo.cc / madc.hi.cc chains.  With r < 2^255 (both
+// fields) t < 2r holds after every step, so t_8 never carries out.
 __device__ __forceinline__ void merge_product_row(uint32_t t[9], const uint64_t P[8]) {
     uint32_t lo[8], hi[8];
 #pragma unroll
@@ -162,6 +195,31 @@ __device__ __forceinline__ void merge_product_row(uint32_t t[9], const uint64_t 
         : "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]),
           "r"(lo[7]), "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]),
           "r"(hi[6]), "r"(hi[7]));
+}
+
+// first product row (t = 0 before it): t = P_0.lo, P_0.hi + P_1.lo, ...,
+// P_6.hi + P_7.lo, P_7.hi + carry -- one chain, no adds of zero
+__device__ __forceinline__ void merge_first_row(uint32_t t[9], const uint64_t P[8]) {
+    uint32_t lo[8], hi[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        lo[j] = uint32_t(P[j]);
+        hi[j] = uint32_t(P[j] >> 32);
+    }
+    t[0] = lo[0];
+    asm("add.cc.u32  %0, %8, %16;\n\t"
+        "addc.cc.u32 %1, %9, %17;\n\t"
+        "addc.cc.u32 %2, %10, %18;\n\t"
+        "addc.cc.u32 %3, %11, %19;\n\t"
+        "addc.cc.u32 %4, %12, %20;\n\t"
+        "addc.cc.u32 %5, %13, %21;\n\t"
+        "addc.cc.u32 %6, %14, %22;\n\t"
+        "addc.u32    %7, %15, 0;"
+        : "=r"(t[1]), "=r"(t[2]), "=r"(t[3]), "=r"(t[4]), "=r"(t[5]), "=r"(t[6]), "=r"(t[7]),
+          "=r"(t[8])
+        : "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]),
+          "r"(hi[7]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]),
+          "r"(lo[7]));
 }
 
 // addend-form product merge: with P_j = a_j b_i + t_j,
@@ -215,14 +273,20 @@ __device__ __forceinline__ void merge_reduce(uint32_t t[9], const uint64_t Q[8])
 }
 
 // Product-row / reduction-row forms (build-time choice, see the comment above):
-//   0: product rows without addend, reduction rows with the 64-bit addend
+//   0: the first product row is a single chain (t = 0 before it), product rows
+//      1..6 without addend, the last product row and every reduction row with
+//      the 64-bit addend (shipped)
 //   1: neither row uses the addend (all merging on the ALU pipe)
-//   2: both rows use the addend
+//   2: every row uses the addend
 #ifndef ZKNTT_MUL_FORM
 #define ZKNTT_MUL_FORM 0
 #endif
 
-// r = a * b * 2^-256 mod p; a, b canonical; r may alias a or b
+// r = a * b * 2^-256 mod p, canonical.  a must be canonical; b may be any
+// value below 2^256: with t <= 2r - 1, a <= r - 1 and b_i, m <= 2^32 - 1 an
+// outer step gives (t + a b_i + m r) / 2^32 <= 2r - 1 whatever b is, and the
+// final value is below r b / 2^256 + r < 2r, so one conditional subtraction
+// canonicalises it.  r may alias a or b.
 template <class F>
 __device__ __forceinline__ void mul(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
     const uint32_t P[8] = {F::P0, F::P1, F::P2, F::P3, F::P4, F::P5, F::P6, F::P7};
@@ -233,7 +297,11 @@ __device__ __forceinline__ void mul(uint32_t r[8], const uint32_t a[8], const ui
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         uint64_t X[8];
-        if (ZKNTT_MUL_FORM == 2) {
+        if (ZKNTT_MUL_FORM == 0 && i == 0) {
+#pragma unroll
+            for (int j = 0; j < 8; j++) X[j] = uint64_t(a[j]) * bb[0];
+            merge_first_row(t, X);
+        } else if (ZKNTT_MUL_FORM == 2 || (ZKNTT_MUL_FORM == 0 && i == 7)) {
 #pragma unroll
             for (int j = 0; j < 8; j++) X[j] = uint64_t(a[j]) * bb[i] + t[j];
             merge_addend_row(t, X);

@@ -19,7 +19,10 @@
 // cp.async.  Stages 0..K-3 run as a loop: each thread takes butterflies
 // (x, y) -> (x + y, (x - y) w) from shared memory and writes them back, so the
 // loop body holds a single inlined Montgomery product and stays resident in
-// the instruction cache.  The last two stages run as one radix-4 step per
+// the instruction cache.  The difference x - y is formed as x + r - y with no
+// conditional correction: it only feeds the product, as its limb-scanned
+// operand, which may be any value below 2^256 (the product's output is
+// canonical either way).  The last two stages run as one radix-4 step per
 // thread on four neighbouring rows, and the scaled elements are then written
 // to global memory.  All sizes (K, C, the stride) are runtime values: one
 // kernel per field serves every digit size.
@@ -231,7 +234,7 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
                 lds_elem(px, s_lo, s_hi, q0);
                 lds_elem(py, s_lo, s_hi, q1);
                 ldg_elem(pw, ws + 2 * size_t(j));
-                sub<F>(pt, px, py);
+                sub_lazy<F>(pt, px, py);
                 add<F>(px, px, py);
             };
             if (active) prepare(tid, x, t, w, s0, s1);
@@ -240,7 +243,7 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
                 uint32_t x2[8], t2[8], w2[8], n0 = 0, n1 = 0;
                 if (nb < (CN >> 1)) prepare(nb, x2, t2, w2, n0, n1);
                 uint32_t y[8];
-                mul<F>(y, t, w);
+                mul<F>(y, w, t);
                 sts_elem(s_lo, s_hi, s0, x);
                 sts_elem(s_lo, s_hi, s1, y);
 #pragma unroll
@@ -271,11 +274,11 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
             }
 #pragma unroll
             for (int k = 0; k < IL; k++) {
-                sub<F>(t[k], x[k], y[k]);
+                sub_lazy<F>(t[k], x[k], y[k]);
                 add<F>(x[k], x[k], y[k]);
             }
 #pragma unroll
-            for (int k = 0; k < IL; k++) mul<F>(y[k], t[k], w[k]);
+            for (int k = 0; k < IL; k++) mul<F>(y[k], w[k], t[k]);
 #pragma unroll
             for (int k = 0; k < IL; k++) {
                 sts_elem(s_lo, s_hi, s0[k], x[k]);
@@ -305,9 +308,9 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
             add<F>(x0, x0, x2);
 #pragma unroll
             for (int k = 0; k < 8; k++) x2[k] = t[k];
-            sub<F>(t, x1, x3);
+            sub_lazy<F>(t, x1, x3);
             add<F>(x1, x1, x3);
-            mul<F>(x3, t, w4);
+            mul<F>(x3, w4, t);
             // stage K-1: pairs (0,1), (2,3), twiddle 1
             sub<F>(t, x0, x1);
             add<F>(x0, x0, x1);

@@ -1286,7 +1286,7 @@ zkntt_status zkntt_field_info(zkntt_field field, uint32_t modulus[8], uint32_t g
 zkntt_status zkntt_field_op(zkntt_field field, int op, const void *d_a, const void *d_b, void *d_c,
                             size_t n, void *stream) {
     if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
-    if (op < 0 || op > 2) return ZKNTT_EINVAL;
+    if (op < 0 || op > 3) return ZKNTT_EINVAL;
     if (n == 0) return ZKNTT_OK;
     if (bad_ptr(d_a) || bad_ptr(d_b) || bad_ptr(d_c)) return ZKNTT_EINVAL;
     DeviceInfo *dev;
