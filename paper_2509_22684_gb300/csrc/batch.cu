@@ -20,7 +20,8 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
 // its own.
 template <class F>
 __device__ __noinline__ void batch_tile(const PassArgs &a, uint4 *smem, uint32_t tile) {
-    run_tile<F, 1>(a, smem, tile, pass_threads(a.K, a.log_cols));
+    const uint32_t nt = pass_threads(a.K, a.log_cols);
+    run_tile<F, 1>(a, smem, tile, nt < BATCH_THREADS ? nt : BATCH_THREADS);
 }
 
 // ctrl[0]: next work item, ctrl[1]: abort word; done[s]: tiles retired per
