@@ -297,11 +297,11 @@ def extras(zk, torch, field: str, stream, peak_imad: float, hbm_gbs: float) -> d
     return out
 
 
-def serve_bench(zk, torch, field: str, n_requests: int, load: float) -> dict:
+def serve_bench(zk, torch, field: str, n_requests: int, loads, solo_log_n=None) -> dict:
     """Served NTT stream: Poisson arrivals, log_n uniform on 12..24, kinds
-    uniform over {NTT, iNTT, coset NTT, coset iNTT}; offered load = `load` x the
-    measured serial capacity; continuous batching vs serial plain execution on
-    the same trace."""
+    uniform over {NTT, iNTT, coset NTT, coset iNTT}; for each offered load
+    (a fraction of the measured serial capacity), continuous batching vs
+    serial plain execution on the same trace."""
     import numpy as np
     from paper_2509_22684_gb300.serve import Engine, GpuExecutor, Request, serve_serial
     from workloads import KINDS, poisson_trace, uniform_elements
@@ -322,23 +322,74 @@ def serve_bench(zk, torch, field: str, n_requests: int, load: float) -> dict:
             p.execute(x, y, stream=cur)
         svc[L] = timed(lambda: p.execute(x, y, stream=cur), cur, 5) / 5 / 1e3
     mean_svc = sum(svc.values()) / len(svc)
-    rate = load / mean_svc
-    trace = poisson_trace(5000, n_requests, rate, 12, 24)
-    mk = lambda: [Request(i, q.arrival_s, field, q.log_n, q.kind) for i, q in enumerate(trace)]
-    eng = Engine(ex, budget_bytes=int(torch.cuda.mem_get_info()[0] * 0.5), streams=2, max_batch_jobs=64)
-    _, st = eng.run(mk())
 
     def run_one(r):
         x = pool[(r.field, r.log_n)]
         ex.plan(r.field, r.log_n, r.kind).execute(x, torch.empty_like(x), stream=cur)
         cur.synchronize()
-    _, ser = serve_serial(mk(), run_one)
+    out = {"requests": n_requests, "serial_capacity_per_s": round(1 / mean_svc, 1),
+           "solo_log_n": solo_log_n}
+    for load in loads:
+        rate = load / mean_svc
+        trace = poisson_trace(5000, n_requests, rate, 12, 24)
+        mk = lambda: [Request(i, q.arrival_s, field, q.log_n, q.kind) for i, q in enumerate(trace)]
+        eng = Engine(ex, budget_bytes=int(torch.cuda.mem_get_info()[0] * 0.5), streams=2,
+                     max_batch_jobs=64, solo_log_n=solo_log_n)
+        _, st = eng.run(mk())
+        _, ser = serve_serial(mk(), run_one)
+        out[f"load_{load}"] = {"offered_rate_per_s": round(rate, 1),
+                               "batched": st.as_dict(), "serial": ser.as_dict(),
+                               "p50_speedup": round(ser.p50_ms / st.p50_ms, 3),
+                               "p99_speedup": round(ser.p99_ms / st.p99_ms, 3),
+                               "throughput_ratio": round(st.melem_s / ser.melem_s, 3)}
     ex.close()
-    return {"requests": n_requests, "offered_rate_per_s": round(rate, 1), "load": load,
-            "serial_capacity_per_s": round(1 / mean_svc, 1),
-            "batched": st.as_dict(), "serial": ser.as_dict(),
-            "p99_speedup": round(ser.p99_ms / st.p99_ms, 3),
-            "throughput_ratio": round(st.melem_s / ser.melem_s, 3)}
+    return out
+
+
+def sweep(args) -> None:
+    """One JSON line per (field, kind, log_n, twiddle mode): the full grid of
+    single-transform configurations, device-resident inputs, CUDA-event
+    timing after warm-up (rank 0 only, no other output)."""
+    import numpy as np
+    import torch
+
+    import paper_2509_22684_gb300 as zk
+    from workloads import KINDS, uniform_elements
+    stream = torch.cuda.current_stream()
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak_imad = sms * IMAD_LANES_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    sizes = [int(v) for v in args.sweep_sizes.split(",")]
+    for field in ("bls12_381_fr", "bn254_fr"):
+        _, g, _ = zk.field_info(field)
+        for L in sizes:
+            X = uniform_elements(FIELD_R[field], 1 << L, 2000 + L)
+            x = torch.from_numpy(X.view(np.int32)).cuda()
+            y = torch.empty_like(x)
+            for kind in KINDS:
+                for mode in ("precomp", "otf"):
+                    with zk.Plan(field, L, inverse=kind.endswith("intt"),
+                                 coset_shift=g if kind.startswith("coset") else None,
+                                 twiddle_mode=mode) as p:
+                        scr = torch.empty(max(8, p.scratch_bytes() // 4), dtype=torch.int32,
+                                          device="cuda")
+                        f = lambda: p.execute_scratch(x, y, scr, stream=stream)
+                        for _ in range(3):
+                            f()
+                        steps = 20 if L <= 22 else 5
+                        ms = timed(f, stream, steps) / steps
+                        d = p.describe()
+                        # coset and inverse add one product per element to the
+                        # algorithmic count (the pre- or post-scale)
+                        mults = butterfly_mults(L) + ((1 << L) if kind != "ntt" else 0)
+                        print(json.dumps({"field": field, "kind": kind, "log_n": L, "mode": mode,
+                                          "ms": round(ms, 4), "melem_s": round((1 << L) / ms / 1e3, 1),
+                                          "alu_frac": round(mults * IMAD_PER_MUL / (ms / 1e3) / peak_imad, 4),
+                                          "digits": d["digits"],
+                                          "table_mib": round(d["table_bytes"] / 2**20, 1)}), flush=True)
+                        del scr
+            del x, y
+    zk.sync_status(stream)
 
 
 def run_ours(args, world, rank, local):
@@ -461,7 +512,9 @@ def run_ours(args, world, rank, local):
                                   "sample": f"C oracle (oracle/cpu_ntt.c) forward NTT 2^{L}, {reps} run(s), {el:.1f} s"}
     if rank == 0 and not args.no_extras:
         result["extras"] = extras(zk, torch, field, stream, peak_imad, hbm_gbs)
-        result["extras"]["serving"] = serve_bench(zk, torch, field, args.serve_requests, args.serve_load)
+        loads = [float(v) for v in args.serve_loads.split(",") if v]
+        result["extras"]["serving"] = serve_bench(zk, torch, field, args.serve_requests, loads,
+                                                  args.serve_solo_log_n)
     if rank == 0:
         print(json.dumps(result), flush=True)
 
@@ -524,7 +577,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
-    ap.add_argument("--serve-load", type=float, default=0.8)
+    ap.add_argument("--serve-loads", default="0.5,0.8,0.95",
+                    help="offered loads, as fractions of the serial capacity")
+    ap.add_argument("--serve-solo-log-n", type=int, default=20,
+                    help="served requests of at least 2^this run as plain transforms")
+    ap.add_argument("--sweep", action="store_true",
+                    help="print one line per field x kind x size x twiddle mode instead")
+    ap.add_argument("--sweep-sizes", default="16,20,22,24,26")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -532,6 +591,9 @@ def main():
         world = int(os.environ.get("WORLD_SIZE", "1"))
         rank = int(os.environ.get("RANK", "0"))
         run_reference(args, world, rank)
+        return
+    if args.sweep:
+        sweep(args)
         return
     world, rank, local = dist_init(args)
     try:

@@ -13,6 +13,13 @@ into the next persistent batch launch:
   unstarted requests (up to ``max_batch_jobs``) go out as ONE
   ``zkntt_execute_batch`` launch on that stream; with two streams, a batch
   formed from late arrivals overlaps the previous one on the device;
+* solo launches: a request of 2^solo_log_n elements or more (when the engine
+  is given ``solo_log_n``), or a batch that would hold a single request, runs
+  as a plain transform instead (an executor's ``launch_solo``): a large
+  transform fills the GPU by itself and runs faster through the plain pass
+  kernels, and a lone small one skips the batch launch's setup.  Large
+  requests keep their arrival order among themselves; small ones behind a
+  large one at the head of the queue may go out first, in the next batch;
 * completion: each request retires as soon as its own transform is done (the
   launch writes a per-transform completion word to host-mapped memory), which
   returns its memory to the budget; the stream is reused once the launch's
@@ -96,7 +103,7 @@ class Engine:
     """Continuous-batching scheduler over an executor (see module docstring)."""
 
     def __init__(self, executor, budget_bytes: int, streams: int = 2, max_batch_jobs: int = 64,
-                 clock=time.perf_counter, idle_sleep_s: float = 20e-6):
+                 clock=time.perf_counter, idle_sleep_s: float = 20e-6, solo_log_n: int | None = None):
         if streams < 1 or max_batch_jobs < 1 or budget_bytes <= 0:
             raise ValueError("bad engine configuration")
         self.ex = executor
@@ -105,6 +112,22 @@ class Engine:
         self.max_batch_jobs = max_batch_jobs
         self.clock = clock
         self.idle_sleep_s = idle_sleep_s
+        self.solo_log_n = solo_log_n
+        self.can_solo = hasattr(executor, "launch_solo")
+
+    def _is_big(self, r: Request) -> bool:
+        return self.can_solo and self.solo_log_n is not None and r.log_n >= self.solo_log_n
+
+    def _next_launch(self, ready: deque) -> tuple[list[Request], bool]:
+        """Requests for the next launch and whether it is a solo launch."""
+        if self._is_big(ready[0]):
+            return [ready.popleft()], True
+        take, skipped = [], []
+        while ready and len(take) < self.max_batch_jobs:
+            r = ready.popleft()
+            (skipped if self._is_big(r) else take).append(r)
+        ready.extendleft(reversed(skipped))    # large ones keep their place
+        return take, self.can_solo and len(take) == 1
 
     def run(self, requests, realtime: bool = True) -> tuple[list[Request], ServeStats]:
         """Serve `requests` (arrival times relative to the start).  With
@@ -161,11 +184,11 @@ class Engine:
             # launch: everything ready goes out on an idle stream
             while ready and free_streams:
                 stream = free_streams.pop(0)
-                take = [ready.popleft() for _ in range(min(len(ready), self.max_batch_jobs))]
+                take, solo = self._next_launch(ready)
                 launch = self.clock() - t0
                 for r in take:
                     r.launch_s = launch
-                token = self.ex.launch(take, stream)
+                token = self.ex.launch_solo(take[0], stream) if solo else self.ex.launch(take, stream)
                 inflight.append((token, stream, take, list(take)))
                 batches += 1
                 batch_sizes.append(len(take))
@@ -212,8 +235,9 @@ def serve_serial(requests, run_one, clock=time.perf_counter, realtime: bool = Tr
 
 class GpuExecutor:
     """Executor over the library: resident plans and input vectors, one
-    persistent batch launch per call (shortest transforms first), per-request
-    completion words in host-mapped memory, a CUDA event per launch."""
+    persistent batch launch per call (shortest transforms first) or one plain
+    transform per solo call, per-request completion words in host-mapped
+    memory for batches, a CUDA event per launch."""
 
     def __init__(self, device=0, streams: int = 2, input_pool=None, keep_outputs: bool = True,
                  flag_slots: int = 4096):
@@ -269,13 +293,27 @@ class GpuExecutor:
                                      self.epoch, stream=s)
         ev = torch.cuda.Event()
         ev.record(s)
-        return ev
+        return ev, False
+
+    def launch_solo(self, r: Request, stream_index: int):
+        """One request as a plain transform (zkntt_execute); it is finished
+        when the launch's event has completed."""
+        torch = self.torch
+        s = self.streams[stream_index]
+        x = self.input_for(r)
+        with torch.cuda.stream(s):
+            r.out = torch.empty_like(x)
+        self.plan(r.field, r.log_n, r.kind).execute(x, r.out, stream=s)
+        ev = torch.cuda.Event()
+        ev.record(s)
+        return ev, True
 
     def done(self, token) -> bool:
-        return token.query()
+        return token[0].query()
 
     def finished(self, token, r: Request) -> bool:
-        return self.flags[r._slot] == r._epoch
+        ev, solo = token
+        return ev.query() if solo else self.flags[r._slot] == r._epoch
 
     def release(self, r: Request):
         if not self.keep_outputs:

@@ -12,7 +12,8 @@ pytestmark = pytest.mark.gpu
 FMAP = {"bls12_381_fr": fld.BLS12_381, "bn254_fr": fld.BN254}
 
 
-def test_served_mix_matches_solo_and_oracle():
+@pytest.mark.parametrize("solo_log_n", [None, 15])
+def test_served_mix_matches_solo_and_oracle(solo_log_n):
     import paper_2509_22684_gb300 as zk
     from paper_2509_22684_gb300.serve import Engine, GpuExecutor, Request
     trace = poisson_trace(5000, 80, 20000.0, lmin=10, lmax=16)
@@ -24,7 +25,8 @@ def test_served_mix_matches_solo_and_oracle():
         r.payload = to_dev(uniform_elements(F.r, 1 << q.log_n, q.seed))
         reqs.append(r)
     ex = GpuExecutor(streams=2, keep_outputs=True)
-    done, st = Engine(ex, budget_bytes=1 << 28, streams=2, max_batch_jobs=16).run(reqs)
+    done, st = Engine(ex, budget_bytes=1 << 28, streams=2, max_batch_jobs=16,
+                      solo_log_n=solo_log_n).run(reqs)
     zk.sync_status()
     assert st.requests == len(reqs)
     assert st.batches < len(reqs)          # requests were batched together

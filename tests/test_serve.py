@@ -113,3 +113,48 @@ def test_small_requests_retire_before_the_large_one_in_their_batch():
     big = [r for r in done if r.rid == 0][0]
     small = [r for r in done if r.rid != 0]
     assert all(r.finish_s < big.finish_s for r in small)
+
+
+class SoloFakeExecutor(FakeExecutor):
+    """FakeExecutor that also runs single requests as plain launches."""
+
+    def __init__(self, **kw):
+        super().__init__(**kw)
+        self.solo = []
+
+    def launch_solo(self, r, stream):
+        self.solo.append(r.rid)
+        return self.launch([r], stream)
+
+
+def test_large_requests_run_solo_in_arrival_order():
+    reqs = _trace(count=300, rate=50000.0, lmin=10, lmax=18)
+    ex = SoloFakeExecutor(per_elem_s=1e-9, overhead_s=1e-4)
+    done, st = Engine(ex, budget_bytes=1 << 32, streams=2, max_batch_jobs=16, solo_log_n=16).run(reqs)
+    assert st.requests == len(reqs)
+    big = {r.rid for r in reqs if r.log_n >= 16}
+    assert big and big <= set(ex.solo)                      # every large one ran alone
+    for _, rids in ex.launched:                             # and never inside a batch
+        if len(rids) > 1:
+            assert not big & set(rids)
+    order = sorted((r for r in reqs if r.log_n >= 16), key=lambda r: (r.arrival_s, r.rid))
+    first_launch = {rid: k for k, (_, rids) in enumerate(ex.launched) for rid in rids}
+    ks = [first_launch[r.rid] for r in order]
+    assert ks == sorted(ks)                                 # large ones keep arrival order
+    launched = [rid for _, rids in ex.launched for rid in rids]
+    assert sorted(launched) == sorted(r.rid for r in reqs)  # each launched exactly once
+
+
+def test_single_request_batches_become_solo_launches():
+    reqs = [Request(i, 0.01 * i, "bls12_381_fr", 10, "ntt") for i in range(5)]
+    ex = SoloFakeExecutor(per_elem_s=1e-9, overhead_s=1e-5)
+    done, st = Engine(ex, budget_bytes=1 << 30, streams=1).run(reqs)
+    assert st.requests == 5
+    assert sorted(ex.solo) == list(range(5))                # spaced arrivals: one at a time
+
+
+def test_without_launch_solo_everything_is_batched():
+    reqs = _trace(count=100, rate=50000.0, lmin=10, lmax=18)
+    ex = FakeExecutor(per_elem_s=1e-9, overhead_s=1e-4)
+    done, st = Engine(ex, budget_bytes=1 << 32, streams=2, solo_log_n=12).run(reqs)
+    assert st.requests == len(reqs)
