@@ -41,7 +41,8 @@ typedef struct {
     u64 wmax[4];   /* Montgomery form of g^((r-1)/2^s) */
 } field_t;
 
-static field_t FIELDS[2];
+#define NFIELDS 3
+static field_t FIELDS[NFIELDS];
 static int fields_ready = 0;
 static pthread_mutex_t init_lock = PTHREAD_MUTEX_INITIALIZER;
 
@@ -178,13 +179,16 @@ static void field_setup(field_t *F, const u64 r[4], u64 g) {
 static void fields_init(void) {
     pthread_mutex_lock(&init_lock);
     if (!fields_ready) {
-        /* BLS12-381 scalar field and BN254 scalar field (standard moduli). */
+        /* BLS12-381, BN254 and BLS12-377 scalar fields (standard moduli). */
         static const u64 bls[4] = {0xffffffff00000001ULL, 0x53bda402fffe5bfeULL,
                                    0x3339d80809a1d805ULL, 0x73eda753299d7d48ULL};
         static const u64 bn[4] = {0x43e1f593f0000001ULL, 0x2833e84879b97091ULL,
                                   0xb85045b68181585dULL, 0x30644e72e131a029ULL};
+        static const u64 bls377[4] = {0x0a11800000000001ULL, 0x59aa76fed0000001ULL,
+                                      0x60b44d1e5c37b001ULL, 0x12ab655e9a2ca556ULL};
         field_setup(&FIELDS[0], bls, 7);
         field_setup(&FIELDS[1], bn, 5);
+        field_setup(&FIELDS[2], bls377, 22);
         fields_ready = 1;
     }
     pthread_mutex_unlock(&init_lock);
@@ -371,7 +375,7 @@ static int ntt_core(const field_t *F, int log_n, int inverse, const u64 *shift,
 }
 
 static int check_args(int field, int log_n) {
-    if (field < 0 || field > 1) return 1;
+    if (field < 0 || field >= NFIELDS) return 1;
     fields_init();
     if (log_n < 0 || log_n > FIELDS[field].s || log_n > 30) return 1;
     return 0;
@@ -396,13 +400,13 @@ int zo_threads_default(void) {
 }
 
 int zo_two_adicity(int field) {
-    if (field < 0 || field > 1) return -1;
+    if (field < 0 || field >= NFIELDS) return -1;
     fields_init();
     return FIELDS[field].s;
 }
 
 int zo_root(int field, int log_n, int inverse, uint32_t *out) {
-    if (field < 0 || field > 1) return 1;
+    if (field < 0 || field >= NFIELDS) return 1;
     fields_init();
     if (log_n < 0 || log_n > FIELDS[field].s) return 1;
     u64 w[4];
@@ -412,7 +416,7 @@ int zo_root(int field, int log_n, int inverse, uint32_t *out) {
 }
 
 int zo_mont_mul(int field, const uint32_t *a, const uint32_t *b, uint32_t *out) {
-    if (field < 0 || field > 1) return 1;
+    if (field < 0 || field >= NFIELDS) return 1;
     fields_init();
     u64 x[4], y[4], z[4];
     load(x, a);
@@ -439,7 +443,7 @@ int zo_ntt(int field, int log_n, int inverse, const uint32_t *shift_mont,
 
 /* out = sum_j c_j x^j (Horner), all Montgomery form */
 int zo_eval(int field, uint64_t n, const uint32_t *coeffs, const uint32_t *x_mont, uint32_t *out) {
-    if (field < 0 || field > 1) return 1;
+    if (field < 0 || field >= NFIELDS) return 1;
     fields_init();
     const field_t *F = &FIELDS[field];
     u64 x[4], acc[4] = {0, 0, 0, 0}, c[4];

@@ -8,13 +8,15 @@ Everything is plain Python integers (arbitrary precision).  Field operations
 return values in [0, r), as the paper states for its finite fields
 (Section II, "Background on ZKP": results of field operations lie in [0, p)).
 
-The paper names BLS12-381 (Section II) and its scalar field F_r as the NTT
-input field; BN254 F_r is the second field of the workload.  Neither the
-generator nor the root of unity is printed in the paper; the readings used are
+The paper names BLS12-381 and BLS12-377 (Section II); the scalar field F_r
+of BLS12-381 is the NTT input field, BN254 F_r is the second field of the
+workload, and BLS12-377 F_r the third.  Neither the generator nor the root of
+unity is printed in the paper; the readings used are
 
-* the multiplicative generator g is 7 for BLS12-381 F_r and 5 for BN254 F_r
-  (checked here: g^((r-1)/q) != 1 for every prime q | r - 1 that we can
-  factor off, and g is a quadratic non-residue);
+* the multiplicative generator g is 7 for BLS12-381 F_r, 5 for BN254 F_r and
+  22 for BLS12-377 F_r (checked by the tests: g is a quadratic non-residue,
+  g^((r-1)/q) != 1 for every prime q | r - 1 that trial division finds, and
+  for BLS12-377 F_r, whose r - 1 is fully factored, for every prime factor);
 * the primitive 2^s-th root is omega_max = g^((r-1)/2^s) with s the 2-adicity
   of r - 1, and omega_n = omega_max^(2^(s-L)) for n = 2^L (Section II-B only
   asks for "a primitive n-th root of unity");
@@ -27,6 +29,7 @@ from dataclasses import dataclass, field as dc_field
 
 BLS12_381_FR = 0x73EDA753299D7D483339D80809A1D80553BDA402FFFE5BFEFFFFFFFF00000001
 BN254_FR = 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001
+BLS12_377_FR = 0x12AB655E9A2CA55660B44D1E5C37B00159AA76FED00000010A11800000000001
 
 LIMBS = 8
 LIMB_BITS = 32
@@ -101,13 +104,14 @@ class Field:
 
 BLS12_381 = Field("bls12_381_fr", BLS12_381_FR, 7)
 BN254 = Field("bn254_fr", BN254_FR, 5)
-FIELDS = {f.name: f for f in (BLS12_381, BN254)}
-FIELD_IDS = {"bls12_381_fr": 0, "bn254_fr": 1}
+BLS12_377 = Field("bls12_377_fr", BLS12_377_FR, 22)
+FIELDS = {f.name: f for f in (BLS12_381, BN254, BLS12_377)}
+FIELD_IDS = {"bls12_381_fr": 0, "bn254_fr": 1, "bls12_377_fr": 2}
 
 
 def get(name_or_field) -> Field:
     if isinstance(name_or_field, Field):
         return name_or_field
     if isinstance(name_or_field, int):
-        return (BLS12_381, BN254)[name_or_field]
+        return (BLS12_381, BN254, BLS12_377)[name_or_field]
     return FIELDS[name_or_field]

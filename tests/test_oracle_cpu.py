@@ -7,7 +7,7 @@ from oracle import field as fld
 from oracle import ntt_ref as ref
 from workloads import limbs_to_ints, uniform_elements
 
-FIELDS = [fld.BLS12_381, fld.BN254]
+FIELDS = [fld.BLS12_381, fld.BN254, fld.BLS12_377]
 IDS = [f.name for f in FIELDS]
 
 

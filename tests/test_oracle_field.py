@@ -17,7 +17,12 @@ def _golden():
             line = line.split("#", 1)[0].strip()
             if not line:
                 continue
-            name, key, val = line.split()
+            parts = line.split()
+            if parts[1] == "factor":           # name factor p e (a list)
+                out.setdefault(parts[0], {}).setdefault("factors", []).append(
+                    (int(parts[2], 0), int(parts[3], 0)))
+                continue
+            name, key, val = parts
             out.setdefault(name, {})[key] = int(val, 0)
     return out
 
@@ -47,7 +52,7 @@ def _is_probable_prime(n, rounds=40):
     return True
 
 
-@pytest.mark.parametrize("F", [fld.BLS12_381, fld.BN254], ids=lambda f: f.name)
+@pytest.mark.parametrize("F", [fld.BLS12_381, fld.BN254, fld.BLS12_377], ids=lambda f: f.name)
 def test_modulus_matches_published_definition(F):
     g = _golden()[F.name]
     assert F.r == g["r"]
@@ -56,7 +61,7 @@ def test_modulus_matches_published_definition(F):
     assert _is_probable_prime(F.r)
 
 
-@pytest.mark.parametrize("F", [fld.BLS12_381, fld.BN254], ids=lambda f: f.name)
+@pytest.mark.parametrize("F", [fld.BLS12_381, fld.BN254, fld.BLS12_377], ids=lambda f: f.name)
 def test_two_adicity(F):
     g = _golden()[F.name]
     assert F.s == g["two_adicity"]
@@ -64,7 +69,7 @@ def test_two_adicity(F):
     assert ((F.r - 1) >> F.s) % 2 == 1
 
 
-@pytest.mark.parametrize("F", [fld.BLS12_381, fld.BN254], ids=lambda f: f.name)
+@pytest.mark.parametrize("F", [fld.BLS12_381, fld.BN254, fld.BLS12_377], ids=lambda f: f.name)
 def test_generator_is_non_residue_and_root_has_exact_order(F):
     r = F.r
     # Euler's criterion: g is a quadratic non-residue, so g^((r-1)/2^s) has order exactly 2^s
@@ -80,7 +85,7 @@ def test_generator_is_non_residue_and_root_has_exact_order(F):
         assert wl * F.root(L, inverse=True) % r == 1
 
 
-@pytest.mark.parametrize("F", [fld.BLS12_381, fld.BN254], ids=lambda f: f.name)
+@pytest.mark.parametrize("F", [fld.BLS12_381, fld.BN254, fld.BLS12_377], ids=lambda f: f.name)
 def test_generator_small_factor_orders(F):
     """g^((r-1)/q) != 1 for the small prime factors q of r - 1 we can find by
     trial division, so g is not confined to a subgroup of index q."""
@@ -99,7 +104,7 @@ def test_generator_small_factor_orders(F):
         assert pow(F.g, (r - 1) // q, r) != 1
 
 
-@pytest.mark.parametrize("F", [fld.BLS12_381, fld.BN254], ids=lambda f: f.name)
+@pytest.mark.parametrize("F", [fld.BLS12_381, fld.BN254, fld.BLS12_377], ids=lambda f: f.name)
 def test_montgomery_constants(F):
     r = F.r
     assert F.R == (1 << 256) % r
@@ -115,11 +120,31 @@ def test_montgomery_constants(F):
         assert F.from_mont(F.mont_mul(F.to_mont(a), F.to_mont(b))) == a * b % r
 
 
-def test_bls12_381_modulus_low_limb_structure():
-    """r = 1 mod 2^32 for BLS12-381 F_r (the low limb is 1, r' = 2^32 - 1);
-    the GPU path is allowed to exploit this, so pin it."""
-    assert fld.BLS12_381.r % (1 << 32) == 1
-    assert fld.BLS12_381.rprime == 0xFFFFFFFF
+def test_bls12_modulus_low_limb_structure():
+    """r = 1 mod 2^32 for the BLS12-381 and BLS12-377 scalar fields (the low
+    limb is 1, r' = 2^32 - 1); the GPU path is allowed to exploit this, so pin
+    it."""
+    for F in (fld.BLS12_381, fld.BLS12_377):
+        assert F.r % (1 << 32) == 1
+        assert F.rprime == 0xFFFFFFFF
+
+
+def test_bls12_377_generator_has_full_order():
+    """r - 1 of BLS12-377 F_r is completely factored in the golden file, so
+    g = 22 is checked to generate the whole multiplicative group:
+    g^((r-1)/q) != 1 for every prime q | r - 1."""
+    F = fld.BLS12_377
+    facs = _golden()[F.name]["factors"]
+    prod = 1
+    for q, e in facs:
+        assert _is_probable_prime(q)
+        prod *= q ** e
+    assert prod == F.r - 1
+    for q, _ in facs:
+        assert pow(F.g, (F.r - 1) // q, F.r) != 1
+    # and a non-generator is rejected by the same check (11 is a non-residue
+    # of smaller order), so the check is not vacuous
+    assert any(pow(11, (F.r - 1) // q, F.r) == 1 for q, _ in facs)
 
 
 def test_moduli_follow_from_curve_parameters():
@@ -128,3 +153,5 @@ def test_moduli_follow_from_curve_parameters():
     assert fld.BLS12_381.r == x ** 4 - x ** 2 + 1
     u = g["bn254_fr"]["u"]
     assert fld.BN254.r == 36 * u ** 4 + 36 * u ** 3 + 18 * u ** 2 + 6 * u + 1
+    x = g["bls12_377_fr"]["x"]
+    assert fld.BLS12_377.r == x ** 4 - x ** 2 + 1

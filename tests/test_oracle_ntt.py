@@ -11,7 +11,7 @@ from oracle import field as fld
 from oracle import ntt_ref as ref
 from workloads import uniform_elements, limbs_to_ints
 
-FIELDS = [fld.BLS12_381, fld.BN254]
+FIELDS = [fld.BLS12_381, fld.BN254, fld.BLS12_377]
 IDS = [f.name for f in FIELDS]
 
 

@@ -19,7 +19,7 @@ def test_splitmix64_reference_values():
 
 
 def test_uniform_matches_scalar_statement():
-    for F in (fld.BLS12_381, fld.BN254):
+    for F in (fld.BLS12_381, fld.BN254, fld.BLS12_377):
         X = uniform_elements(F.r, 257, 77)
         assert limbs_to_ints(X) == uniform_elements_scalar(F.r, 257, 77)
 
