@@ -35,6 +35,7 @@ METRIC = "NTT Melem/s (BLS12-381 Fr, 2^24 forward) + % int/HBM roofline"
 FIELD_R = {
     "bls12_381_fr": 0x73EDA753299D7D483339D80809A1D80553BDA402FFFE5BFEFFFFFFFF00000001,
     "bn254_fr": 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001,
+    "bls12_377_fr": 0x12AB655E9A2CA55660B44D1E5C37B00159AA76FED00000010A11800000000001,
 }
 
 
@@ -360,7 +361,7 @@ def sweep(args) -> None:
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak_imad = sms * IMAD_LANES_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     sizes = [int(v) for v in args.sweep_sizes.split(",")]
-    for field in ("bls12_381_fr", "bn254_fr"):
+    for field in args.sweep_fields.split(","):
         _, g, _ = zk.field_info(field)
         for L in sizes:
             X = uniform_elements(FIELD_R[field], 1 << L, 2000 + L)
@@ -584,6 +585,7 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="print one line per field x kind x size x twiddle mode instead")
     ap.add_argument("--sweep-sizes", default="16,20,22,24,26")
+    ap.add_argument("--sweep-fields", default="bls12_381_fr,bn254_fr,bls12_377_fr")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -10,8 +10,8 @@
  *     forward:  A_k = sum_j (a_j g^j) w^(jk)
  *     inverse:  a_j = g^-j * n^-1 * sum_k A_k w^(-jk).
  * w = w_max^(2^(s - log_n)) where w_max = g0^((r-1)/2^s), g0 the field's
- * multiplicative generator (7 for BLS12-381 F_r, 5 for BN254 F_r) and s the
- * 2-adicity of r - 1 (32 and 28).
+ * multiplicative generator (7 for BLS12-381 F_r, 5 for BN254 F_r, 22 for
+ * BLS12-377 F_r) and s the 2-adicity of r - 1 (32, 28 and 47).
  *
  * Element layout (Section II: field elements as word-sized limbs): 8 x uint32
  * little-endian limbs = 32 bytes, Montgomery form X = x * 2^256 mod r,
@@ -37,7 +37,9 @@
 extern "C" {
 #endif
 
-typedef enum { ZKNTT_BLS12_381_FR = 0, ZKNTT_BN254_FR = 1 } zkntt_field;
+/* The scalar fields F_r of BLS12-381 (the curve the paper evaluates, Section
+ * II), BN254, and BLS12-377 (also named in Section II). */
+typedef enum { ZKNTT_BLS12_381_FR = 0, ZKNTT_BN254_FR = 1, ZKNTT_BLS12_377_FR = 2 } zkntt_field;
 typedef enum { ZKNTT_FORWARD = 0, ZKNTT_INVERSE = 1 } zkntt_dir;
 typedef enum {
     ZKNTT_OK = 0,
@@ -80,9 +82,9 @@ typedef struct {
 /*
  * Create a plan for one transform size/direction on the current CUDA device.
  *   out          receives the plan handle (not written on failure)
- *   field        ZKNTT_BLS12_381_FR or ZKNTT_BN254_FR
- *   log_n        1 .. 28 for both fields (device-memory bound; the fields'
- *                2-adicities are 32 and 28)
+ *   field        ZKNTT_BLS12_381_FR, ZKNTT_BN254_FR or ZKNTT_BLS12_377_FR
+ *   log_n        1 .. 28 for every field (device-memory bound; the fields'
+ *                2-adicities are 32, 28 and 47)
  *   dir          ZKNTT_FORWARD or ZKNTT_INVERSE
  *   coset_shift  NULL for a plain transform, else the shift g as 8 uint32
  *                Montgomery-form limbs (host memory, read during the call);

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("ZKNTT_LIB") or os.path.join(HERE, "libzkntt.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
-FIELDS = {"bls12_381_fr": 0, "bn254_fr": 1}
+FIELDS = {"bls12_381_fr": 0, "bn254_fr": 1, "bls12_377_fr": 2}
 TWIDDLE_MODES = {"auto": 0, "precomp": 1, "otf": 2}
 
 

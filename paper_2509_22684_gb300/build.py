@@ -23,7 +23,8 @@ OBJ = os.path.join(HERE, "_build") if LIB == os.path.join(HERE, "libzkntt.so") e
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}",
          "-Xptxas", "-warn-spills"]
-UNITS = ["batch.cu", "kernels_bls12_381.cu", "kernels_bn254.cu", "zkntt.cu", "tuner.cu"]
+UNITS = ["batch.cu", "kernels_bls12_381.cu", "kernels_bn254.cu", "kernels_bls12_377.cu", "zkntt.cu",
+         "tuner.cu"]
 
 
 def _nvcc() -> str:

@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, BATCH_MIN_BLOCKS)
         const BatchSeg &sg = tab.seg[s_seg];
         const uint32_t tile = s_item - sg.first_item;
         if (sg.field == 0) batch_tile<FrBLS12_381>(sg.a, smem, tile);
-        else batch_tile<FrBN254>(sg.a, smem, tile);
+        else if (sg.field == 1) batch_tile<FrBN254>(sg.a, smem, tile);
+        else batch_tile<FrBLS12_377>(sg.a, smem, tile);
         // run_tile ends with a block barrier: every store of the tile is issued
         if (threadIdx.x == 0) {
             __threadfence();

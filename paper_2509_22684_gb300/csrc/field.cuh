@@ -11,7 +11,7 @@
 //   32-bit multiply-add (IMAD) the dominant instruction (Section IV-B-2).  Every
 //   carry chain is a single asm statement of add.cc / addc.cc instructions, so
 //   the carry flag never has to survive between statements.  For r < 2^255
-//   (both fields here) the running value t stays below 2r after each outer
+//   (all three fields here) the running value t stays below 2r after each outer
 //   step, so nine limbs suffice and no tenth carry limb is kept.
 // * add / sub: the paper measures the conditional-reduction branches as 70.5%
 //   of FF_add latency (Section IV-B-1) and 52-56% branch efficiency (Section
@@ -38,6 +38,14 @@ struct FrBN254 {
                               P4 = 0x8181585du, P5 = 0xb85045b6u, P6 = 0xe131a029u, P7 = 0x30644e72u;
     static constexpr uint32_t RP = 0xefffffffu;
     static constexpr int ID = 1;
+};
+
+// BLS12-377 F_r (253 bits; r = 1 mod 2^32 as for BLS12-381, so m = -t_0)
+struct FrBLS12_377 {
+    static constexpr uint32_t P0 = 0x00000001u, P1 = 0x0a118000u, P2 = 0xd0000001u, P3 = 0x59aa76feu,
+                              P4 = 0x5c37b001u, P5 = 0x60b44d1eu, P6 = 0x9a2ca556u, P7 = 0x12ab655eu;
+    static constexpr uint32_t RP = 0xffffffffu;
+    static constexpr int ID = 2;
 };
 
 // ---------------------------------------------------------------------------
@@ -164,7 +172,7 @@ __device__ __forceinline__ void sub_lazy(uint32_t r[8], const uint32_t a[8], con
 // asm chains are opaque to the compiler, so it gets its own single chain
 // instead of adding zeros.  Measured on GB300, BLS12-381 F_r: 58.3 G
 // products/s, against 55.7 with every product row in the two-chain form and
-// 43 for separate mad.lo.cc / madc.hi.cc chains.  With r < 2^255 (both
+// 43 for separate mad.lo.cc / madc.hi.cc chains.  With r < 2^255 (all
 // fields) t < 2r holds after every step, so t_8 never carries out.
 __device__ __forceinline__ void merge_product_row(uint32_t t[9], const uint64_t P[8]) {
     uint32_t lo[8], hi[8];

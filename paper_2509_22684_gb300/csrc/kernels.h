@@ -19,6 +19,10 @@ struct FieldKernels {
 
 const FieldKernels &kernels_bls12_381();
 const FieldKernels &kernels_bn254();
+const FieldKernels &kernels_bls12_377();
+
+// fields with kernels, ids 0 .. NUM_FIELDS - 1 (the zkntt_field values)
+constexpr int NUM_FIELDS = 3;
 const void *batch_kernel_ptr();
 
 }  // namespace zkntt

@@ -1,0 +1,22 @@
+// kernels_bls12_377.cu -- kernel instantiations for the BLS12-377 scalar field.
+#include "aux_kernels.cuh"
+#include "kernels.h"
+#include "ntt_pass.cuh"
+
+namespace zkntt {
+
+const FieldKernels &kernels_bls12_377() {
+    using F = FrBLS12_377;
+    static const FieldKernels k = {
+        {nullptr, (const void *)&ntt_pass_kernel<F, 1>, (const void *)&ntt_pass_kernel<F, 2>,
+         (const void *)&ntt_pass_kernel<F, 3>, (const void *)&ntt_pass_kernel<F, 4>},
+        (const void *)&gen_powers_kernel<F>,
+        (const void *)&gen_twiddle_kernel<F>,
+        (const void *)&field_op_kernel<F>,
+        (const void *)&pointwise_kernel<F>,
+        (const void *)&mulbench_kernel<F>,
+    };
+    return k;
+}
+
+}  // namespace zkntt

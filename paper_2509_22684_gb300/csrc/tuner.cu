@@ -153,7 +153,7 @@ using namespace zkntt;
 
 extern "C" zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_candidates,
                                    zkntt_tune_result *best) {
-    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (field < 0 || field >= NUM_FIELDS) return ZKNTT_EINVAL;
     if (log_n < 1 || log_n > 28 || max_candidates < 1) return ZKNTT_EINVAL;
     struct Cand {
         zkntt_plan_options o;

@@ -208,10 +208,13 @@ HostField make_field(uint32_t gen) {
 const HostField &host_field(int id) {
     static const HostField bls = make_field<FrBLS12_381>(7);
     static const HostField bn = make_field<FrBN254>(5);
-    return id == 0 ? bls : bn;
+    static const HostField bls377 = make_field<FrBLS12_377>(22);
+    return id == 0 ? bls : id == 1 ? bn : bls377;
 }
 
-const FieldKernels &field_kernels(int id) { return id == 0 ? kernels_bls12_381() : kernels_bn254(); }
+const FieldKernels &field_kernels(int id) {
+    return id == 0 ? kernels_bls12_381() : id == 1 ? kernels_bn254() : kernels_bls12_377();
+}
 
 uint32_t rev_bits(uint32_t x, int bits) {
     uint32_t r = 0;
@@ -238,7 +241,7 @@ zkntt_status device_info(DeviceInfo **out) {
     DeviceInfo &d = g_devices[dev];
     if (!d.init) {
         ZK_CHECK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
-        for (int f = 0; f < 2; f++)
+        for (int f = 0; f < NUM_FIELDS; f++)
             for (int ilp = 1; ilp <= 4; ilp++)
                 ZK_CHECK(cudaFuncSetAttribute(field_kernels(f).pass[ilp],
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
@@ -583,6 +586,8 @@ PassArgs pass_args(const zkntt_plan_s *P, int i, const void *in, void *out) {
     return a;
 }
 
+bool valid_field(int field) { return field >= 0 && field < NUM_FIELDS; }
+
 bool bad_ptr(const void *p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 31u); }
 
 bool partial_overlap(const void *a, const void *b, size_t bytes) {
@@ -643,7 +648,7 @@ zkntt_status create_plan(zkntt_plan *out, zkntt_field field, int log_n, zkntt_di
                          const uint32_t *coset_shift, const zkntt_plan_options *opts,
                          const E8 *extra) {
     if (!out) return ZKNTT_EINVAL;
-    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (!valid_field(field)) return ZKNTT_EINVAL;
     if (dir != ZKNTT_FORWARD && dir != ZKNTT_INVERSE) return ZKNTT_EINVAL;
     const HostField &F = host_field(field);
     if (log_n < 1 || log_n > std::min(F.s, 28)) return ZKNTT_EINVAL;
@@ -1083,7 +1088,7 @@ zkntt_status zkntt_flags_destroy(uint32_t *host_view) {
 
 zkntt_status zkntt_groth16_h(zkntt_field field, int log_n, const void *d_a, const void *d_b,
                              const void *d_c, void *d_h, void *d_scratch, int fused, void *stream) {
-    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (!valid_field(field)) return ZKNTT_EINVAL;
     if (log_n < 1 || log_n > 28) return ZKNTT_EINVAL;
     if (bad_ptr(d_a) || bad_ptr(d_b) || bad_ptr(d_c) || bad_ptr(d_h) || bad_ptr(d_scratch))
         return ZKNTT_EINVAL;
@@ -1161,7 +1166,7 @@ zkntt_status zkntt_groth16_graph_create(zkntt_graph *out, zkntt_field field, int
                                         const void *d_a, const void *d_b, const void *d_c, void *d_h,
                                         void *d_scratch, void *stream) {
     if (!out) return ZKNTT_EINVAL;
-    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (!valid_field(field)) return ZKNTT_EINVAL;
     if (log_n < 1 || log_n > 28) return ZKNTT_EINVAL;
     if (!stream) return ZKNTT_EINVAL;  // the legacy default stream cannot be captured
     // everything that allocates or synchronises happens before the capture
@@ -1274,7 +1279,7 @@ zkntt_status zkntt_selftest_timeout(int timeout_ms, void *stream) {
 
 zkntt_status zkntt_field_info(zkntt_field field, uint32_t modulus[8], uint32_t generator_mont[8],
                               int *two_adicity) {
-    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (!valid_field(field)) return ZKNTT_EINVAL;
     const HostField &F = host_field(field);
     if (!F.ok) return ZKNTT_ECUDA;
     if (modulus) memcpy(modulus, F.p.data(), 32);
@@ -1285,7 +1290,7 @@ zkntt_status zkntt_field_info(zkntt_field field, uint32_t modulus[8], uint32_t g
 
 zkntt_status zkntt_field_op(zkntt_field field, int op, const void *d_a, const void *d_b, void *d_c,
                             size_t n, void *stream) {
-    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (!valid_field(field)) return ZKNTT_EINVAL;
     if (op < 0 || op > 3) return ZKNTT_EINVAL;
     if (n == 0) return ZKNTT_OK;
     if (bad_ptr(d_a) || bad_ptr(d_b) || bad_ptr(d_c)) return ZKNTT_EINVAL;
@@ -1299,7 +1304,7 @@ zkntt_status zkntt_field_op(zkntt_field field, int op, const void *d_a, const vo
 
 zkntt_status zkntt_pointwise(zkntt_field field, const void *d_a, const void *d_b, const void *d_c,
                              const uint32_t *z_mont, void *d_h, size_t n, void *stream) {
-    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (!valid_field(field)) return ZKNTT_EINVAL;
     if (!z_mont) return ZKNTT_EINVAL;
     if (n == 0) return ZKNTT_OK;
     if (bad_ptr(d_a) || bad_ptr(d_b) || bad_ptr(d_c) || bad_ptr(d_h)) return ZKNTT_EINVAL;
@@ -1314,7 +1319,7 @@ zkntt_status zkntt_pointwise(zkntt_field field, const void *d_a, const void *d_b
 
 zkntt_status zkntt_mulbench(zkntt_field field, int blocks, int threads, int iters, void *d_sink,
                             void *stream) {
-    if (field != ZKNTT_BLS12_381_FR && field != ZKNTT_BN254_FR) return ZKNTT_EINVAL;
+    if (!valid_field(field)) return ZKNTT_EINVAL;
     if (blocks < 1 || threads < 32 || threads > 256 || iters < 1 || !d_sink) return ZKNTT_EINVAL;
     void *args[] = {&iters, &d_sink};
     return from_cuda(cudaLaunchKernel(field_kernels(field).mulbench, dim3(blocks), dim3(threads),

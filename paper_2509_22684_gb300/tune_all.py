@@ -22,11 +22,12 @@ def main():
     ap.add_argument("--candidates", type=int, default=40)
     ap.add_argument("--large-candidates", type=int, default=16,
                     help="candidate budget for log_n >= 25")
+    ap.add_argument("--fields", default="bls12_381_fr,bn254_fr,bls12_377_fr")
     args = ap.parse_args()
     os.environ["ZKNTT_TUNE_CACHE"] = os.path.abspath(args.out)
     import paper_2509_22684_gb300 as zk
     t0 = time.time()
-    for field in ("bls12_381_fr", "bn254_fr"):
+    for field in args.fields.split(","):
         _, _, s = zk.field_info(field)
         for inverse in (False, True):
             for L in range(args.lmin, min(args.lmax, s, 28) + 1):

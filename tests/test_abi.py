@@ -52,6 +52,8 @@ def test_host_side_validation_without_gpu(lib):
     h = ctypes.c_void_p()
     # field, log_n, direction and null handle are rejected before any CUDA call
     assert lib.zkntt_plan_create(ctypes.byref(h), 7, 10, 0, None) == N.EINVAL
+    assert lib.zkntt_plan_create(ctypes.byref(h), 3, 10, 0, None) == N.EINVAL
+    assert lib.zkntt_plan_create(ctypes.byref(h), 2, 29, 0, None) == N.EINVAL
     assert lib.zkntt_plan_create(ctypes.byref(h), 0, 0, 0, None) == N.EINVAL
     assert lib.zkntt_plan_create(ctypes.byref(h), 1, 29, 0, None) == N.EINVAL
     assert lib.zkntt_plan_create(ctypes.byref(h), 0, 33, 0, None) == N.EINVAL
@@ -73,6 +75,6 @@ def test_host_side_validation_without_gpu(lib):
 def test_field_info_without_gpu(lib):
     from oracle import field as fld
     import paper_2509_22684_gb300 as zk
-    for F in (fld.BLS12_381, fld.BN254):
+    for F in (fld.BLS12_381, fld.BN254, fld.BLS12_377):
         m, g, s = zk.field_info(F.name)
         assert m == F.r and g == F.to_mont(F.g) and s == F.s

@@ -12,7 +12,7 @@ from workloads import batch_jobs, uniform_elements
 from gpu_util import first_mismatch, rand_dev, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
-FMAP = {"bls12_381_fr": fld.BLS12_381, "bn254_fr": fld.BN254}
+FMAP = {"bls12_381_fr": fld.BLS12_381, "bn254_fr": fld.BN254, "bls12_377_fr": fld.BLS12_377}
 
 
 def _oracle(F, X, inverse=False, shift=None):
@@ -21,10 +21,14 @@ def _oracle(F, X, inverse=False, shift=None):
     return cpu.ntt(F, X, inverse=inverse, shift_mont=shift)
 
 
-def test_batch_uneven_mixed_fields_matches_oracle_and_solo():
+@pytest.mark.parametrize("fields", [("bls12_381_fr", "bn254_fr"),
+                                    ("bls12_381_fr", "bn254_fr", "bls12_377_fr")],
+                         ids=["two_fields", "three_fields"])
+def test_batch_uneven_mixed_fields_matches_oracle_and_solo(fields):
     import torch
     import paper_2509_22684_gb300 as zk
-    jobs = batch_jobs(4000, count=64, lmin=10, lmax=20)
+    jobs = batch_jobs(4000, count=64, lmin=10, lmax=20, fields=fields)
+    assert {j.field for j in jobs} == set(fields)
     plans, xs, outs, hosts = [], [], [], []
     for j in jobs:
         F = FMAP[j.field]
@@ -63,7 +67,7 @@ def test_batch_in_place_and_order_independence():
         p.close()
 
 
-@pytest.mark.parametrize("F", [fld.BLS12_381, fld.BN254], ids=lambda f: f.name)
+@pytest.mark.parametrize("F", [fld.BLS12_381, fld.BN254, fld.BLS12_377], ids=lambda f: f.name)
 @pytest.mark.parametrize("L", [4, 10, 13, 16])
 @pytest.mark.parametrize("fused", [False, True])
 def test_groth16_matches_oracle(F, L, fused):

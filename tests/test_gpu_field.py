@@ -9,7 +9,7 @@ from workloads import ints_to_limbs, limbs_to_ints, splitmix64, uniform_elements
 from gpu_util import to_dev, to_host
 
 pytestmark = pytest.mark.gpu
-FIELDS = [fld.BLS12_381, fld.BN254]
+FIELDS = [fld.BLS12_381, fld.BN254, fld.BLS12_377]
 
 
 def _edge_values(F):

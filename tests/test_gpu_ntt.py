@@ -11,7 +11,7 @@ from oracle import ntt_ref as ref
 from gpu_util import first_mismatch, rand_dev, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
-FIELDS = [fld.BLS12_381, fld.BN254]
+FIELDS = [fld.BLS12_381, fld.BN254, fld.BLS12_377]
 KINDS = ["ntt", "intt", "coset_ntt", "coset_intt"]
 
 
