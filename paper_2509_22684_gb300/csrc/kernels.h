@@ -23,6 +23,8 @@ const FieldKernels &kernels_bls12_377();
 
 // fields with kernels, ids 0 .. NUM_FIELDS - 1 (the zkntt_field values)
 constexpr int NUM_FIELDS = 3;
+// pass-kernel schedule variants, 1 .. NUM_VARIANTS (the plan's `ilp` option)
+constexpr int NUM_VARIANTS = 4;
 const void *batch_kernel_ptr();
 
 }  // namespace zkntt

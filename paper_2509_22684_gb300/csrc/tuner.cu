@@ -165,7 +165,7 @@ extern "C" zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, 
         splits(log_n, p, sp);
         for (auto &d : sp)
             for (int mode : {ZKNTT_TWIDDLE_PRECOMP, ZKNTT_TWIDDLE_OTF})
-                for (int ilp : {1, 2, 3, 4})
+                for (int ilp = 1; ilp <= NUM_VARIANTS; ilp++)
                 for (int cap = 3; cap >= 1; cap--) {
                     if (p == 1 && (mode == ZKNTT_TWIDDLE_OTF || cap != 3)) continue;
                     Cand c;

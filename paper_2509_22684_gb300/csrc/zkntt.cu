@@ -242,7 +242,7 @@ zkntt_status device_info(DeviceInfo **out) {
     if (!d.init) {
         ZK_CHECK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
         for (int f = 0; f < NUM_FIELDS; f++)
-            for (int ilp = 1; ilp <= 4; ilp++)
+            for (int ilp = 1; ilp <= NUM_VARIANTS; ilp++)
                 ZK_CHECK(cudaFuncSetAttribute(field_kernels(f).pass[ilp],
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
         ZK_CHECK(cudaFuncSetAttribute(batch_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -416,7 +416,7 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
                 cols[i] = te.log_cols[i];
             }
             mode = te.mode;
-            if (te.ilp >= 1 && te.ilp <= 4) ilp = te.ilp;
+            if (te.ilp >= 1 && te.ilp <= NUM_VARIANTS) ilp = te.ilp;
         }
     }
     if (opts && opts->num_passes > 0) {
@@ -435,7 +435,7 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
     }
     if (opts && opts->twiddle_mode) mode = opts->twiddle_mode;
     if (opts && opts->ilp) {
-        if (opts->ilp < 1 || opts->ilp > 4) return ZKNTT_EINVAL;
+        if (opts->ilp < 1 || opts->ilp > NUM_VARIANTS) return ZKNTT_EINVAL;
         ilp = opts->ilp;
     }
     if (mode != ZKNTT_TWIDDLE_OTF) mode = ZKNTT_TWIDDLE_PRECOMP;
