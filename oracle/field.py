@@ -6,7 +6,7 @@ does.
 
 Everything is plain Python integers (arbitrary precision).  Field operations
 return values in [0, r), as the paper states for its finite fields
-(Section II, "Background on ZKP": results of field operations lie in [0, p)).
+(Section II, background on ZKPs: results of field operations lie in [0, p)).
 
 The paper names BLS12-381 and BLS12-377 (Section II); the scalar field F_r
 of BLS12-381 is the NTT input field, BN254 F_r is the second field of the
@@ -19,7 +19,7 @@ unity is printed in the paper; the readings used are
   for BLS12-377 F_r, whose r - 1 is fully factored, for every prime factor);
 * the primitive 2^s-th root is omega_max = g^((r-1)/2^s) with s the 2-adicity
   of r - 1, and omega_n = omega_max^(2^(s-L)) for n = 2^L (Section II-B only
-  asks for "a primitive n-th root of unity");
+  asks only for a primitive root of unity of order n);
 * Montgomery radix R = 2^256 (8 limbs of 32 bits, Section II: "word-sized
   limbs").
 """

@@ -11,11 +11,12 @@ Definitions followed (arxiv 2509.22684):
 * Radix-2 Cooley-Tukey, Section II-B and Fig. 3(b): n/2 butterflies per
   stage, log2 n stages, butterfly (x, y) -> (x + y*w, x - y*w).
 * Inverse transform: the paper treats it as the same computation (Section
-  II-B, "INTT and NTT"); the reading used is omega^-1 followed by the factor
+  II-B, where NTT and INTT are discussed together); the reading used is
+  omega^-1 followed by the factor
   n^-1, so that inverse(forward(a)) = a.
 * Coset transforms (Groth16, Fig. 2): forward with shift g is NTT(a_j g^j);
   inverse with shift g multiplies the inverse transform's output j by g^-j.
-* Groth16 H (Fig. 2 and Section IV-A, "seven NTT operations"): three inverse
+* Groth16 H (Fig. 2 and Section IV-A, seven transforms in all): three inverse
   NTTs of the evaluation vectors a, b, c; three coset NTTs; the pointwise
   (A*B - C)/Z on the coset, where Z(x) = x^n - 1 takes the constant value
   g^n - 1 at every coset point g*omega^i; one coset inverse NTT.

@@ -16,34 +16,29 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     return v;
 }
 
-// One out-of-line tile routine per field, so each is register-allocated on
-// its own.
-template <class F>
-__device__ __noinline__ void batch_tile(const PassArgs &a, uint4 *smem, uint32_t tile) {
-    const uint32_t nt = pass_threads(a.K, a.log_cols);
-    run_tile<F, 1>(a, smem, tile, nt < BATCH_THREADS ? nt : BATCH_THREADS);
-}
-
 // ctrl[0]: next work item, ctrl[1]: abort word; done[s]: tiles retired per
 // segment; status: sticky per-device error word read by the host.  Thread 0
 // claims the block's next work item while the current tile is processed, so
-// the atomic's round trip is hidden behind the tile.
+// the atomic's round trip is hidden behind the tile; the claimed index waits in
+// shared memory, which keeps the tile routine's register budget (64, for four
+// blocks of 256 per SM) free of bookkeeping.  One kernel per field: the tile
+// routine is inlined and its constants are immediates.
+template <class F>
 __global__ void __launch_bounds__(BATCH_THREADS, BATCH_MIN_BLOCKS)
     batch_kernel(const __grid_constant__ BatchTable tab, uint32_t *ctrl, uint32_t *done,
                  uint32_t *status) {
     extern __shared__ uint4 smem[];
-    __shared__ uint32_t s_item, s_seg, s_stop;
-    uint32_t next = 0;
-    if (threadIdx.x == 0) next = atomicAdd(&ctrl[0], 1u);
+    __shared__ uint32_t s_item, s_seg, s_stop, s_next;
+    if (threadIdx.x == 0) s_next = atomicAdd(&ctrl[0], 1u);
     for (;;) {
         if (threadIdx.x == 0) {
             uint32_t stop = 0, segi = 0;
-            const uint32_t item = next;
+            const uint32_t item = s_next;
             if (item >= tab.total_items || *(volatile uint32_t *)&ctrl[1]) {
                 stop = 1;
             } else {
-                next = atomicAdd(&ctrl[0], 1u);  // claim ahead
-                uint32_t lo = 0, hi = tab.nseg;  // last segment with first_item <= item
+                s_next = atomicAdd(&ctrl[0], 1u);  // claim ahead
+                uint32_t lo = 0, hi = tab.nseg;    // last segment with first_item <= item
                 while (hi - lo > 1) {
                     const uint32_t mid = (lo + hi) >> 1;
                     if (tab.seg[mid].first_item <= item) lo = mid;
@@ -76,9 +71,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, BATCH_MIN_BLOCKS)
         if (s_stop) break;
         const BatchSeg &sg = tab.seg[s_seg];
         const uint32_t tile = s_item - sg.first_item;
-        if (sg.field == 0) batch_tile<FrBLS12_381>(sg.a, smem, tile);
-        else if (sg.field == 1) batch_tile<FrBN254>(sg.a, smem, tile);
-        else batch_tile<FrBLS12_377>(sg.a, smem, tile);
+        const uint32_t nt = pass_threads(sg.a.K, sg.a.log_cols);
+        run_tile<F, 1>(sg.a, smem, tile, nt < BATCH_THREADS ? nt : BATCH_THREADS);
         // run_tile ends with a block barrier: every store of the tile is issued
         if (threadIdx.x == 0) {
             __threadfence();
@@ -94,6 +88,10 @@ __global__ void __launch_bounds__(BATCH_THREADS, BATCH_MIN_BLOCKS)
     }
 }
 
-const void *batch_kernel_ptr() { return (const void *)&batch_kernel; }
+const void *batch_kernel_ptr(int field) {
+    if (field == 1) return (const void *)&batch_kernel<FrBN254>;
+    if (field == 2) return (const void *)&batch_kernel<FrBLS12_377>;
+    return (const void *)&batch_kernel<FrBLS12_381>;
+}
 
 }  // namespace zkntt

@@ -1,8 +1,8 @@
-// batch.cuh -- persistent kernel running many transforms (uneven sizes, both
-// fields, with dependencies between them) in one launch.
+// batch.cuh -- persistent kernel running many transforms (uneven sizes, with
+// dependencies between them) in one launch per field.
 //
-// The paper finds that the Groth16 prover issues "seven NTT operations, each
-// with multiple kernel launches" (Section IV-A) and that such short kernels run
+// The paper finds that the Groth16 prover runs seven transforms, every one of
+// them as several kernel launches (Section IV-A), and that such short kernels run
 // with sub-optimal launch parameters; it calls for runtime autotuning (Section
 // V-A).  Here every pass of every transform is a segment of tiles; all tiles of
 // all segments form one work list ordered by dependency level.  Resident
@@ -27,13 +27,14 @@ namespace zkntt {
 
 constexpr int BATCH_MAX_SEGMENTS = 160;
 constexpr uint32_t BATCH_THREADS = 256;
-// blocks per SM the register budget is compiled for (80 registers a thread)
-constexpr int BATCH_MIN_BLOCKS = 3;
+// blocks per SM the register budget is compiled for (64 registers a thread)
+constexpr int BATCH_MIN_BLOCKS = 4;
+// resident blocks per SM the tile-width policy counts as one wave
+constexpr int BATCH_WAVE_BLOCKS = 3;
 constexpr uint32_t BATCH_STATUS_TIMEOUT = 4u;  // == ZKNTT_ETIMEOUT
 
 struct BatchSeg {
     PassArgs a;
-    uint32_t field;       // 0 BLS12-381 F_r, 1 BN254 F_r
     uint32_t K;           // digit bits of this pass
     uint32_t first_item;  // index of the segment's first tile in the work list
     int32_t dep[3];       // segments that must be complete first (-1: none)

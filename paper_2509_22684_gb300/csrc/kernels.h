@@ -25,6 +25,6 @@ const FieldKernels &kernels_bls12_377();
 constexpr int NUM_FIELDS = 3;
 // pass-kernel schedule variants, 1 .. NUM_VARIANTS (the plan's `ilp` option)
 constexpr int NUM_VARIANTS = 4;
-const void *batch_kernel_ptr();
+const void *batch_kernel_ptr(int field);
 
 }  // namespace zkntt

@@ -1,8 +1,8 @@
 // ntt_pass.cuh -- one pass of the multi-pass NTT for sm_103a.
 //
 // Decomposition (the four-step identity applied recursively; Section II-B of
-// the paper notes that a block NTT is bounded by shared memory and that
-// "different stages can be processed in batches"):
+// the paper notes that a block NTT is bounded by shared memory and that groups
+// of stages may be run together):
 //   n = 2^L is split into digits k_1 + ... + k_p = L (top digit first).  Pass i
 //   treats the vector as columns: for fixed (hi, lo) the N = 2^K elements at
 //       q = (hi * N + d) * 2^lo_bits + lo,   d = 0..N-1

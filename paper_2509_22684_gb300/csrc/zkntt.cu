@@ -225,8 +225,8 @@ uint32_t rev_bits(uint32_t x, int bits) {
 // ---------------------------------------------------------------------------
 struct DeviceInfo {
     int sms = 0;
-    int batch_blocks_per_sm[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // batch kernel occupancy for
-                                                            // 2^(10+i) bytes of smem
+    // batch kernel occupancy per field for 2^(10+i) bytes of shared memory
+    int batch_blocks_per_sm[NUM_FIELDS][8] = {};
     bool init = false;
     uint32_t *status = nullptr;  // sticky device-side error word
 };
@@ -245,12 +245,15 @@ zkntt_status device_info(DeviceInfo **out) {
             for (int ilp = 1; ilp <= NUM_VARIANTS; ilp++)
                 ZK_CHECK(cudaFuncSetAttribute(field_kernels(f).pass[ilp],
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-        ZK_CHECK(cudaFuncSetAttribute(batch_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      64 * 1024));
-        for (int i = 0; i < 7; i++) {
-            ZK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &d.batch_blocks_per_sm[i], batch_kernel_ptr(), BATCH_THREADS, size_t(1024) << i));
-            d.batch_blocks_per_sm[i] = std::max(d.batch_blocks_per_sm[i], 1);
+        for (int f = 0; f < NUM_FIELDS; f++) {
+            ZK_CHECK(cudaFuncSetAttribute(batch_kernel_ptr(f),
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+            for (int i = 0; i < 7; i++) {
+                ZK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &d.batch_blocks_per_sm[f][i], batch_kernel_ptr(f), BATCH_THREADS,
+                    size_t(1024) << i));
+                d.batch_blocks_per_sm[f][i] = std::max(d.batch_blocks_per_sm[f][i], 1);
+            }
         }
         ZK_CHECK(cudaMalloc(&d.status, sizeof(uint32_t)));
         ZK_CHECK(cudaMemset(d.status, 0, sizeof(uint32_t)));
@@ -691,12 +694,15 @@ struct JobSpec {
     int deps[3] = {-1, -1, -1};                   // jobs whose last pass must finish first
 };
 
-zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
-                          unsigned long long timeout_ns, uint32_t *flags = nullptr,
-                          uint32_t epoch = 0, const std::vector<uint32_t> *job_ids = nullptr) {
+// One persistent launch over jobs of one field (job_ids: completion-word index
+// of each job).
+zkntt_status launch_batch_field(const std::vector<JobSpec> &jobs, cudaStream_t s,
+                                unsigned long long timeout_ns, uint32_t *flags, uint32_t epoch,
+                                const std::vector<uint32_t> &job_ids) {
     DeviceInfo *dev;
     zkntt_status st = device_info(&dev);
     if (st != ZKNTT_OK) return st;
+    const int field = jobs.empty() ? 0 : jobs[0].plan->field;
     struct SegTmp {
         int job, pass, level;
     };
@@ -713,7 +719,7 @@ zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
     // therefore takes the widest tile its digit allows, narrowed toward the
     // plan's own width only while the pass has fewer tiles than one wave of
     // resident blocks (the plan's tables do not depend on the tile width).
-    const uint64_t wave = uint64_t(dev->sms) * BATCH_MIN_BLOCKS;
+    const uint64_t wave = uint64_t(dev->sms) * BATCH_WAVE_BLOCKS;
     auto batch_log_cols = [&](const zkntt_plan_s *P, int i) {
         const PassPlan &ps = P->ps[i];
         const int span = (i == P->passes - 1) ? ps.hi_bits : ps.lo_bits;
@@ -747,11 +753,10 @@ zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
             sg.a.pw_b = static_cast<const uint4 *>(J.pw_b);
             sg.a.pw_c = static_cast<const uint4 *>(J.pw_c);
         }
-        sg.field = uint32_t(P->field);
         sg.K = uint32_t(P->ps[i].K);
         sg.first_item = item;
         sg.ntiles = sg.a.num_tiles;
-        sg.job = job_ids ? (*job_ids)[segs[k].job] : uint32_t(segs[k].job);
+        sg.job = job_ids[segs[k].job];
         sg.signal = (flags && i == P->passes - 1) ? 1u : 0u;
         item += sg.a.num_tiles;
         for (int d = 0; d < 3; d++) {
@@ -801,17 +806,63 @@ zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
         int si = 0;
         while ((size_t(1024) << si) < smem) si++;
         smem = size_t(1024) << si;
-        uint32_t grid = std::min<uint32_t>(item, uint32_t(dev->batch_blocks_per_sm[si]) * dev->sms);
+        // Resident blocks: at most what fits, and no more than splits the
+        // widest dependency level into whole, equal waves -- a level of T tiles
+        // over G blocks otherwise ends in a partial wave with most SMs idle
+        // while the next level waits on it.
+        uint32_t grid = std::min<uint32_t>(item, uint32_t(dev->batch_blocks_per_sm[field][si]) *
+                                                     uint32_t(dev->sms));
+        std::map<int, uint32_t> per_level;
+        for (int k = 0; k < int(segs.size()); k++) per_level[segs[k].level] += tab->seg[k].ntiles;
+        uint32_t widest = 0;
+        for (const auto &kv : per_level) widest = std::max(widest, kv.second);
+        if (grid > 0 && widest > 0) {
+            const uint32_t waves = (widest + grid - 1) / grid;
+            grid = std::min(grid, std::max<uint32_t>((widest + waves - 1) / waves,
+                                                     std::min<uint32_t>(item, dev->sms)));
+        }
         uint32_t *done = ctrl + 2;
         uint32_t *status = dev->status;
         void *args[] = {tab, &ctrl, &done, &status};
         if (e == cudaSuccess && grid > 0)
-            e = cudaLaunchKernel(batch_kernel_ptr(), dim3(grid), dim3(BATCH_THREADS), args, smem, s);
+            e = cudaLaunchKernel(batch_kernel_ptr(field), dim3(grid), dim3(BATCH_THREADS), args,
+                                 smem, s);
     }
     cudaError_t e2 = cudaFreeAsync(ctrl, s);
     delete tab;
     if (e != cudaSuccess) return from_cuda(e);
     return from_cuda(e2);
+}
+
+// Jobs of several fields run as one persistent launch per field, in order of
+// each field's first job, on stream s (a dependency must stay within a field).
+zkntt_status launch_batch(const std::vector<JobSpec> &jobs, cudaStream_t s,
+                          unsigned long long timeout_ns, uint32_t *flags = nullptr,
+                          uint32_t epoch = 0, const std::vector<uint32_t> *job_ids = nullptr) {
+    std::vector<int> order;  // fields in order of first appearance
+    for (const JobSpec &J : jobs)
+        if (std::find(order.begin(), order.end(), J.plan->field) == order.end())
+            order.push_back(J.plan->field);
+    for (int f : order) {
+        std::vector<JobSpec> sub;
+        std::vector<uint32_t> ids;
+        std::vector<int> local(jobs.size(), -1);
+        for (int j = 0; j < int(jobs.size()); j++) {
+            if (jobs[j].plan->field != f) continue;
+            local[j] = int(sub.size());
+            sub.push_back(jobs[j]);
+            ids.push_back(job_ids ? (*job_ids)[j] : uint32_t(j));
+        }
+        for (JobSpec &J : sub)
+            for (int d = 0; d < 3; d++) {
+                if (J.deps[d] < 0) continue;
+                if (local[J.deps[d]] < 0) return ZKNTT_EINVAL;  // dependency across fields
+                J.deps[d] = local[J.deps[d]];
+            }
+        zkntt_status st = launch_batch_field(sub, s, timeout_ns, flags, epoch, ids);
+        if (st != ZKNTT_OK) return st;
+    }
+    return ZKNTT_OK;
 }
 
 unsigned long long batch_timeout_ns() {
@@ -1269,7 +1320,7 @@ zkntt_status zkntt_selftest_timeout(int timeout_ms, void *stream) {
         uint32_t *done = ctrl + 2;
         uint32_t *status = dev->status;
         void *args[] = {tab, &ctrl, &done, &status};
-        e = cudaLaunchKernel(batch_kernel_ptr(), dim3(1), dim3(BATCH_THREADS), args, 64 * 1024, s);
+        e = cudaLaunchKernel(batch_kernel_ptr(0), dim3(1), dim3(BATCH_THREADS), args, 64 * 1024, s);
     }
     if (ctrl) cudaFreeAsync(ctrl, s);
     delete tab;
