@@ -63,6 +63,7 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.zkntt_plan_create(ctypes.byref(h), 0, 10, 0, zero) == N.EINVAL
     assert lib.zkntt_execute(None, None, None, None) == N.EINVAL
     assert lib.zkntt_execute_batch(None, None, -1, None) == N.EINVAL
+    assert lib.zkntt_execute_batch(None, None, 0, None) == N.OK          # empty batch: no-op
     assert lib.zkntt_execute_batch(None, None, 0, None) == N.OK
     assert lib.zkntt_groth16_h(0, 10, None, None, None, None, None, 1, None) == N.EINVAL
     assert lib.zkntt_plan_destroy(None) == N.OK

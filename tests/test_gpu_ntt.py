@@ -116,6 +116,28 @@ def test_2_26_sampled_outputs_and_round_trip(F):
     assert np.array_equal(to_host(z), X)
 
 
+def test_bn254_maximum_size_2_28():
+    """BN254 F_r has 2-adicity 28, so 2^28 is its largest transform (the
+    field's top root of unity is used): outputs at sampled k against the
+    definition (Horner in the C oracle), and inverse(forward(x)) == x over the
+    whole vector, compared on the device (8 GiB per vector)."""
+    import torch
+    F = fld.BN254
+    L = 28
+    assert F.s == L
+    X, x = rand_dev(F, L, 2028)
+    with _plan(F, L, "ntt") as p:
+        y = p.execute(x)
+    w = F.root(L)
+    for k in (1, (1 << L) - 1, 200000003):
+        got = int.from_bytes(to_host(y[k:k + 1]).tobytes(), "little")
+        assert got == cpu.eval_at(F, X, F.to_mont(pow(w, k, F.r))), k
+    del X
+    with _plan(F, L, "intt") as q:
+        z = q.execute(y)
+    assert torch.equal(z, x)
+
+
 def test_round_trip_config1():
     """BLS12-381, n = 2^12, seed 1001: forward then inverse returns the input."""
     F = fld.BLS12_381
