@@ -347,6 +347,36 @@ def serve_bench(zk, torch, field: str, n_requests: int, loads, solo_log_n=None) 
     return out
 
 
+def groth16_only(args) -> None:
+    """Groth16 H at 2^L: the fused persistent launch in a CUDA graph and the
+    seven transforms + pointwise issued separately, both after warm-up, with
+    CUDA events (one JSON line; rank 0 only)."""
+    import numpy as np
+    import torch
+
+    import paper_2509_22684_gb300 as zk
+    from workloads import uniform_elements
+    field, L = args.field, args.groth16
+    stream = torch.cuda.current_stream()
+    a, b, c = (torch.from_numpy(uniform_elements(FIELD_R[field], 1 << L, s).view(np.int32)).cuda()
+               for s in (3001, 3002, 3003))
+    h = torch.empty_like(a)
+    scr = torch.empty((3 << L, 8), dtype=torch.int32, device="cuda")
+    gs = torch.cuda.Stream()
+    graph = zk.Groth16Graph(field, L, a, b, c, h, scr, stream=gs)
+    fused = lambda: graph.launch(stream=stream)
+    sep = lambda: zk.groth16_h(field, L, a, b, c, h=h, scratch=scr, fused=False, stream=stream)
+    out = {"workload": f"groth16_h {field} n=2^{L}", "steps": args.steps, "warmup": args.warmup}
+    for name, f in (("fused_graph_ms", fused), ("separate_ms", sep)):
+        for _ in range(args.warmup):
+            f()
+        out[name] = round(timed(f, stream, args.steps) / args.steps, 4)
+    graph.close()
+    zk.sync_status(stream)
+    out["speedup"] = round(out["separate_ms"] / out["fused_graph_ms"], 3)
+    print(json.dumps(out), flush=True)
+
+
 def sweep(args) -> None:
     """One JSON line per (field, kind, log_n, twiddle mode): the full grid of
     single-transform configurations, device-resident inputs, CUDA-event
@@ -586,6 +616,8 @@ def main():
                     help="print one line per field x kind x size x twiddle mode instead")
     ap.add_argument("--sweep-sizes", default="16,20,22,24,26")
     ap.add_argument("--sweep-fields", default="bls12_381_fr,bn254_fr,bls12_377_fr")
+    ap.add_argument("--groth16", type=int, default=0, metavar="L",
+                    help="time only the Groth16 H sequence at 2^L (fused graph vs separate)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -596,6 +628,9 @@ def main():
         return
     if args.sweep:
         sweep(args)
+        return
+    if args.groth16:
+        groth16_only(args)
         return
     world, rank, local = dist_init(args)
     try:
