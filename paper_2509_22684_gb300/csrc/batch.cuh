@@ -31,6 +31,8 @@ constexpr uint32_t BATCH_THREADS = 256;
 constexpr int BATCH_MIN_BLOCKS = 4;
 // resident blocks per SM the tile-width policy counts as one wave
 constexpr int BATCH_WAVE_BLOCKS = 3;
+// widest batch tile, log2 elements (32 KiB: four blocks per SM fit in shared memory)
+constexpr int BATCH_TILE_BITS = 10;
 constexpr uint32_t BATCH_STATUS_TIMEOUT = 4u;  // == ZKNTT_ETIMEOUT
 
 struct BatchSeg {

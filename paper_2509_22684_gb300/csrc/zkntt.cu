@@ -716,14 +716,17 @@ zkntt_status launch_batch_field(const std::vector<JobSpec> &jobs, cudaStream_t s
     for (int k = 0; k < int(segs.size()); k++) index[{segs[k].job, segs[k].pass}] = k;
     // The batch kernel runs 256 threads a block whatever the tile, so a tile of
     // C x 2^K elements with C x 2^K / 4 < 256 leaves threads idle.  Each pass
-    // therefore takes the widest tile its digit allows, narrowed toward the
-    // plan's own width only while the pass has fewer tiles than one wave of
-    // resident blocks (the plan's tables do not depend on the tile width).
+    // therefore takes the widest tile up to 2^BATCH_TILE_BITS elements (32 KiB,
+    // so four blocks fit an SM's shared memory; an 11-bit digit keeps its
+    // 2^11-element tile), narrowed toward the plan's own width only while the
+    // pass has fewer tiles than one wave of resident blocks (the plan's tables
+    // do not depend on the tile width).
     const uint64_t wave = uint64_t(dev->sms) * BATCH_WAVE_BLOCKS;
     auto batch_log_cols = [&](const zkntt_plan_s *P, int i) {
         const PassPlan &ps = P->ps[i];
         const int span = (i == P->passes - 1) ? ps.hi_bits : ps.lo_bits;
-        int lc = std::max(0, std::min({3, MAX_TILE_BITS - ps.K, span}));
+        const int cap = std::max(BATCH_TILE_BITS, ps.K);
+        int lc = std::max(0, std::min({3, cap - ps.K, span}));
         while (lc > ps.log_cols && (uint64_t(1) << (P->log_n - ps.K - lc)) < wave) lc--;
         return lc;
     };
