@@ -32,6 +32,7 @@ if ROOT not in sys.path:
 IMAD_PER_MUL = 264          # 8 x 32-bit CIOS: 8 x (16 + 1 + 16) multiply-adds
 IMAD_LANES_PER_SM_CLK = 64  # 32-bit integer multiply-add issue rate per SM per clock
 METRIC = "NTT Melem/s (BLS12-381 Fr, 2^24 forward) + % int/HBM roofline"
+FIELD_IDS = {"bls12_381_fr": 0, "bn254_fr": 1, "bls12_377_fr": 2}
 FIELD_R = {
     "bls12_381_fr": 0x73EDA753299D7D483339D80809A1D80553BDA402FFFE5BFEFFFFFFFF00000001,
     "bn254_fr": 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001,
@@ -53,26 +54,46 @@ def measured_peaks() -> dict:
         return {}
 
 
+# the sources the timed pass kernel is compiled from (BLS12-381 instantiation)
+PASS_KERNEL_SOURCES = ("field.cuh", "ntt_pass.cuh", "kernels_bls12_381.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2509_22684_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in PASS_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_hash: str, workload: str):
-    """dram bytes per launch recorded from an ncu capture of the same kernel
-    sources (profiles/ntt_traffic.json); None if absent or stale."""
+def tuned_schedule(field_id: int, log_n: int, direction: int = 0) -> str:
+    """The shipped tuned entry the plan uses (digits, columns, variant,
+    twiddle mode), as a canonical string; "default" if none."""
+    try:
+        with open(os.path.join(ROOT, "paper_2509_22684_gb300", "zkntt_tuned.jsonl")) as f:
+            for line in f:
+                e = json.loads(line)
+                if (e.get("field"), e.get("log_n"), e.get("dir")) == (field_id, log_n, direction):
+                    p = e["passes"]
+                    return json.dumps({"digits": e["digits"][:p], "log_cols": e["log_cols"][:p],
+                                       "ilp": e["ilp"], "mode": e["mode"]}, sort_keys=True)
+    except (OSError, ValueError, KeyError):
+        pass
+    return "default"
+
+
+def recorded_traffic(kernel_hash: str, workload: str, schedule: str):
+    """dram bytes per launch recorded from an ncu capture of the same pass
+    kernel sources running the same schedule (profiles/ntt_traffic.json);
+    None if absent or stale."""
     try:
         with open(os.path.join(ROOT, "profiles", "ntt_traffic.json")) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
     e = rec.get(workload)
-    if not e or e.get("kernel_hash") != kernel_hash:
+    if not e or e.get("kernel_hash") != kernel_hash or e.get("schedule") != schedule:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -500,7 +521,7 @@ def run_ours(args, world, rank, local):
     value = world * n * args.steps / (ms_max / 1e3) / 1e6
     workload = f"{field} forward NTT n=2^{L}"
     khash = kernel_source_hash()
-    traffic = recorded_traffic(khash, workload)
+    traffic = recorded_traffic(khash, workload, tuned_schedule(FIELD_IDS[field], L))
     result = {
         "metric": METRIC,
         "value": round(value, 2),
