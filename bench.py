@@ -99,15 +99,19 @@ def recorded_traffic(kernel_hash: str, workload: str, schedule: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms; only the
+    samples whose timestamps fall inside the timed region count (the nearest
+    later one if the region is shorter than the sampling interval)."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+             "timestamp")
 
     def __init__(self, gpu_index: int):
         self.gpu_index = gpu_index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(prefix="zkntt_clocks_", suffix=".csv")
@@ -115,10 +119,28 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        deadline = time.time() + 3.0        # wait for the sampler's first line
+        while time.time() < deadline and os.path.getsize(self.path) == 0:
+            time.sleep(0.01)
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(s: str):
+        import datetime
+        try:
+            return datetime.datetime.strptime(s.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -132,9 +154,14 @@ class ClockSampler:
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
+                if len(parts) >= 10:
                     rows.append(parts)
         os.unlink(self.path)
+        if self.t0 is not None and self.t1 is not None and rows:
+            stamped = [(self._stamp(r[9]), r) for r in rows]
+            inside = [r for t, r in stamped if t is not None and self.t0 <= t <= self.t1 + 0.01]
+            later = [r for t, r in stamped if t is not None and t > self.t1]
+            rows = inside or later[:1] or rows[-1:]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -477,8 +504,10 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     clocks = ClockSampler(int(os.environ.get("ZKNTT_SMI_INDEX", local)))
     clocks.start()
+    clocks.mark_start()
     ms_total = timed(step, stream, args.steps)
     torch.cuda.synchronize()
+    clocks.mark_end()
     clk = clocks.stop()
     barrier(world)
     ms_max = max_over_ranks(world, ms_total)
