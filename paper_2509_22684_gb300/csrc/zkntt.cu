@@ -257,11 +257,16 @@ zkntt_status device_info(DeviceInfo **out) {
         }
         ZK_CHECK(cudaMalloc(&d.status, sizeof(uint32_t)));
         ZK_CHECK(cudaMemset(d.status, 0, sizeof(uint32_t)));
-        // keep freed stream-ordered scratch in the pool between executions
+        // keep freed stream-ordered scratch in the pool between executions, and
+        // never hand a block freed on one stream to another stream behind an
+        // inserted wait: calls on different streams (the host-buffer path,
+        // concurrent batches) must stay independent; the pool grows instead
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
             uint64_t thr = UINT64_MAX;
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            int no = 0;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
         }
         d.init = true;
     }
