@@ -132,17 +132,22 @@ __device__ __forceinline__ void sub(uint32_t r[8], const uint32_t a[8], const ui
 // (limb-scanned) operand, which may be any value below 2^256.
 template <class F>
 __device__ __forceinline__ void sub_lazy(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
-#pragma unroll
-    for (int i = 0; i < 8; i++) r[i] = a[i];
-    asm("add.cc.u32  %0, %0, %16;\n\t"
-        "addc.cc.u32 %1, %1, %17;\n\t"
-        "addc.cc.u32 %2, %2, %18;\n\t"
-        "addc.cc.u32 %3, %3, %19;\n\t"
-        "addc.cc.u32 %4, %4, %20;\n\t"
-        "addc.cc.u32 %5, %5, %21;\n\t"
-        "addc.cc.u32 %6, %6, %22;\n\t"
-        "addc.u32    %7, %7, %23;\n\t"
-        "sub.cc.u32  %0, %0, %8;\n\t"
+    // r = a + p into fresh registers (a stays live for the caller: no copy),
+    // then r -= b in place
+    asm("add.cc.u32  %0, %8, %16;\n\t"
+        "addc.cc.u32 %1, %9, %17;\n\t"
+        "addc.cc.u32 %2, %10, %18;\n\t"
+        "addc.cc.u32 %3, %11, %19;\n\t"
+        "addc.cc.u32 %4, %12, %20;\n\t"
+        "addc.cc.u32 %5, %13, %21;\n\t"
+        "addc.cc.u32 %6, %14, %22;\n\t"
+        "addc.u32    %7, %15, %23;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
+          "n"(F::P0), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5), "n"(F::P6),
+          "n"(F::P7));
+    asm("sub.cc.u32  %0, %0, %8;\n\t"
         "subc.cc.u32 %1, %1, %9;\n\t"
         "subc.cc.u32 %2, %2, %10;\n\t"
         "subc.cc.u32 %3, %3, %11;\n\t"
@@ -152,9 +157,7 @@ __device__ __forceinline__ void sub_lazy(uint32_t r[8], const uint32_t a[8], con
         "subc.u32    %7, %7, %15;"
         : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
           "+r"(r[7])
-        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]),
-          "n"(F::P0), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5), "n"(F::P6),
-          "n"(F::P7));
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
 }
 
 // ---------------------------------------------------------------------------
