@@ -220,6 +220,28 @@ def cpu_oracle_rate(field: str, log_n: int, budget_s: float, X=None):
     return (reps << log_n) / el / 1e6, threads, reps, el
 
 
+def host_link_gbs(torch, h_in, h_out, d_buf, reps: int = 3):
+    """Pinned host <-> device copy bandwidth (GB/s) for one vector, each
+    direction alone, timed with CUDA events on a side stream."""
+    s = torch.cuda.Stream()
+    out = []
+    for direction in ("h2d", "d2h"):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            for k in range(reps + 1):
+                if k == 1:
+                    e0.record(s)
+                if direction == "h2d":
+                    d_buf.copy_(h_in, non_blocking=True)
+                else:
+                    h_out.copy_(d_buf, non_blocking=True)
+            e1.record(s)
+        e1.synchronize()
+        out.append(round(reps * h_in.numel() * h_in.element_size() / (e0.elapsed_time(e1) / 1e3) / 1e9, 1))
+    return out
+
+
 def timed(fn, stream, steps: int) -> float:
     import torch
     e0 = torch.cuda.Event(enable_timing=True)
@@ -542,6 +564,7 @@ def run_ours(args, world, rank, local):
     ms_e2e = max_over_ranks(world, e2e_run(e2e_steps))
     ok = all(bool(np.array_equal(yh.numpy().view(np.uint32), y.cpu().numpy().view(np.uint32)))
              for yh in yhs)
+    link = host_link_gbs(torch, xh, yhs[0], x)
 
     passes = desc["passes"]
     avg_launch_s = ms_total / 1e3 / (args.steps * passes)
@@ -580,7 +603,11 @@ def run_ours(args, world, rank, local):
                 "h2d_bytes_per_step": 32 * n, "d2h_bytes_per_step": 32 * n,
                 "api": "zkntt_execute_host (pinned host buffers, steps over 4 streams)",
                 "timing": "host wall clock around the steps with device synchronisation on both sides",
-                "matches_device_result": ok},
+                "matches_device_result": ok,
+                # pinned-copy bandwidth of this machine, one direction at a time: the
+                # copies of a step are hidden behind its transform only while
+                # 32n bytes each way take less than the transform
+                "link_h2d_gbs": link[0], "link_d2h_gbs": link[1]},
         "gpu_launches": args.steps * passes,
         "clocks": clk,
     }
