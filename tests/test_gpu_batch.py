@@ -179,3 +179,35 @@ def test_signalled_batch_sets_every_flag_and_matches_oracle():
     for p in plans:
         p.close()
     flags.close()
+
+
+def test_batch_larger_than_one_segment_table_is_split():
+    """64 three-pass transforms are 192 pass segments, more than one persistent
+    launch's table holds (160): the batch runs as consecutive launches and
+    every result still equals the solo execution; the signalled form also
+    marks every transform complete."""
+    import torch
+    import paper_2509_22684_gb300 as zk
+    F = fld.BLS12_381
+    plans, xs, outs = [], [], []
+    for i in range(64):
+        L = 12 + (i % 3)
+        digits = (4, 4, L - 8)
+        plans.append(zk.Plan(F.name, L, inverse=bool(i & 1), digits=digits))
+        xs.append(to_dev(uniform_elements(F.r, 1 << L, 7000 + i)))
+        outs.append(torch.empty_like(xs[-1]))
+    assert sum(p.describe()["passes"] for p in plans) == 192
+    zk.execute_batch(plans, xs, outs)
+    zk.sync_status()
+    for p, x, o in zip(plans, xs, outs):
+        assert np.array_equal(to_host(o), to_host(p.execute(x)))
+    flags = zk.CompletionFlags(64)
+    outs2 = [torch.empty_like(x) for x in xs]
+    zk.execute_batch_signal(plans, xs, outs2, flags, list(range(64)), 9)
+    zk.sync_status()
+    assert all(flags[i] == 9 for i in range(64))
+    for o, o2 in zip(outs, outs2):
+        assert torch.equal(o, o2)
+    flags.close()
+    for p in plans:
+        p.close()
