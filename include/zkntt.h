@@ -76,7 +76,9 @@ typedef struct {
     int ilp;               /* kernel variant: 1 = one butterfly per thread per stage step (3 blocks
                               per SM), 2 = two interleaved butterflies (2 blocks), 3 = one
                               butterfly with registers for 4 blocks, 4 = software-pipelined
-                              stage loop (2 blocks); 0 = auto */
+                              stage loop (2 blocks), 5 = as 3 with twice the threads per
+                              tile (for small transforms); 0 = auto; outside 0..5 ->
+                              ZKNTT_EINVAL */
 } zkntt_plan_options;
 
 /*

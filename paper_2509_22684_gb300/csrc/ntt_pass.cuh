@@ -357,6 +357,13 @@ __host__ __device__ constexpr uint32_t pass_threads(uint32_t K, uint32_t lc) {
                : 256u;
 }
 
+// threads per block for schedule variant v: variant 5 doubles the count (one
+// butterfly per thread per stage), still at most 256
+__host__ __device__ constexpr uint32_t pass_threads_for(uint32_t K, uint32_t lc, int v) {
+    return v == 5 && K >= 2 && pass_threads(K, lc) < 256u ? 2u * pass_threads(K, lc)
+                                                           : pass_threads(K, lc);
+}
+
 // Schedule variants (the plan's `ilp` option):
 //   1: one butterfly per thread per stage step, registers for 3 blocks of 256
 //   2: two interleaved butterflies per thread, registers for 2 blocks
@@ -364,11 +371,15 @@ __host__ __device__ constexpr uint32_t pass_threads(uint32_t K, uint32_t lc) {
 //      elements so four fit in shared memory)
 //   4: software-pipelined stage loop (the product of one butterfly overlaps
 //      the loads and add/subtract of the next), registers for 2 blocks
+//   5: as 3 with twice the threads per tile (one butterfly per thread per
+//      stage; half the threads idle in the radix-4 epilogue): more warps in
+//      flight for transforms too small to fill the GPU
 template <int V> struct PassVariant;
 template <> struct PassVariant<1> { static constexpr int ILP = 1, MIN_BLOCKS = 3; };
 template <> struct PassVariant<2> { static constexpr int ILP = 2, MIN_BLOCKS = 2; };
 template <> struct PassVariant<3> { static constexpr int ILP = 1, MIN_BLOCKS = 4; };
 template <> struct PassVariant<4> { static constexpr int ILP = 0, MIN_BLOCKS = 2; };  // pipelined
+template <> struct PassVariant<5> { static constexpr int ILP = 1, MIN_BLOCKS = 4; };  // 2x threads
 
 template <class F, int V>
 __global__ void __launch_bounds__(256, PassVariant<V>::MIN_BLOCKS) ntt_pass_kernel(const PassArgs a) {

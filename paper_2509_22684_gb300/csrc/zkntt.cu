@@ -484,7 +484,7 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
         ps.ilp = ilp;
         ps.num_tiles = last ? (uint32_t(1) << (ps.hi_bits - lc))
                             : (uint32_t(1) << (ps.hi_bits + ps.lo_bits - lc));
-        ps.threads = int(pass_threads(uint32_t(ps.K), uint32_t(lc)));
+        ps.threads = int(pass_threads_for(uint32_t(ps.K), uint32_t(lc), ilp));
         ps.smem = size_t(32) << (ps.K + lc);
         int nb = 0;
         ZK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(

@@ -175,13 +175,14 @@ def test_argument_errors():
 
 @pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
 @pytest.mark.parametrize("kind", KINDS)
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("digits,cols", [((8, 8), None), ((5, 6, 5), None), ((11, 5), (1, 8)),
                                          ((4, 4, 4, 4), (8, 8, 8, 8)), ((10,), None), ((3,), None),
                                          ((7, 9), (4, 2))])
 def test_kernel_variants(F, kind, variant, digits, cols):
     """Every kernel variant (one or two butterflies per thread, the register
-    budgets, the pipelined loop) gives the same result."""
+    budgets, the pipelined loop, twice the threads per tile) gives the same
+    result."""
     L = sum(digits)
     X, x = rand_dev(F, L, 99 + L)
     with _plan(F, L, kind, digits=digits, cols=cols, ilp=variant) as p:
