@@ -62,7 +62,9 @@ def threads_default() -> int:
 
 def ntt(F, X: np.ndarray, inverse: bool = False, shift_mont: int | None = None,
         threads: int | None = None) -> np.ndarray:
-    """Montgomery-form limbs [n, 8] -> transform, same layout."""
+    """Montgomery-form limbs [n, 8] -> transform, same layout: the C oracle's
+    radix-2 transform (Section II-B; inverse with n^-1, coset with shift^j,
+    as in ntt_ref.ntt)."""
     X = np.ascontiguousarray(X, dtype=np.uint32)
     n = X.shape[0]
     L = n.bit_length() - 1
@@ -76,7 +78,8 @@ def ntt(F, X: np.ndarray, inverse: bool = False, shift_mont: int | None = None,
 
 
 def eval_at(F, coeffs: np.ndarray, x_mont: int) -> int:
-    """sum_j c_j x^j with every value in Montgomery form; returns an int."""
+    """sum_j c_j x^j with every value in Montgomery form (one output of the
+    Section II-B definition when x = w^k); returns an int."""
     coeffs = np.ascontiguousarray(coeffs, dtype=np.uint32)
     xs = _limbs(x_mont)
     out = np.zeros(8, dtype=np.uint32)
@@ -87,6 +90,8 @@ def eval_at(F, coeffs: np.ndarray, x_mont: int) -> int:
 
 
 def groth16_h(F, A, B, C, threads: int | None = None) -> np.ndarray:
+    """The Groth16 H sequence of Fig. 2 (Section IV-A) in the C oracle, on
+    Montgomery-form limbs."""
     A, B, C = (np.ascontiguousarray(v, dtype=np.uint32) for v in (A, B, C))
     n = A.shape[0]
     out = np.empty_like(A)
@@ -98,6 +103,7 @@ def groth16_h(F, A, B, C, threads: int | None = None) -> np.ndarray:
 
 
 def root(F, log_n: int, inverse: bool = False) -> int:
+    """The C oracle's primitive 2^log_n-th root (Section II-B), Montgomery form."""
     out = np.zeros(8, dtype=np.uint32)
     if lib().zo_root(_fid(F), log_n, int(inverse), _p(out)):
         raise ValueError("bad root request")
@@ -105,10 +111,12 @@ def root(F, log_n: int, inverse: bool = False) -> int:
 
 
 def mont_mul(F, a: int, b: int) -> int:
+    """The C oracle's Montgomery product a b 2^-256 mod r (FF_mul, Section IV-B)."""
     out = np.zeros(8, dtype=np.uint32)
     lib().zo_mont_mul(_fid(F), _p(_limbs(a)), _p(_limbs(b)), _p(out))
     return int.from_bytes(out.tobytes(), "little")
 
 
 def two_adicity(F) -> int:
+    """The C oracle's 2-adicity of r - 1."""
     return int(lib().zo_two_adicity(_fid(F)))

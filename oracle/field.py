@@ -37,6 +37,8 @@ R_BITS = LIMBS * LIMB_BITS  # 256
 
 
 def two_adicity(r: int) -> int:
+    """Largest s with 2^s | r - 1: the largest power-of-two transform the
+    field supports (Section II-B needs a primitive n-th root of unity)."""
     s = 0
     m = r - 1
     while m % 2 == 0:
@@ -69,24 +71,32 @@ class Field:
 
     # --- plain field operations (Python big ints; results in [0, r)) -------
     def add(self, a: int, b: int) -> int:
+        """FF_add (Section IV-B-1): a + b reduced to [0, r)."""
         return (a + b) % self.r
 
     def sub(self, a: int, b: int) -> int:
+        """FF_sub (Section IV-B-1): a - b reduced to [0, r)."""
         return (a - b) % self.r
 
     def mul(self, a: int, b: int) -> int:
+        """FF_mul (Section IV-B) by definition: a * b reduced to [0, r)."""
         return (a * b) % self.r
 
     def inv(self, a: int) -> int:
+        """a^-1 mod r (needed for n^-1 and the coset inverse, Section II-B and
+        Fig. 2)."""
         if a % self.r == 0:
             raise ZeroDivisionError("0 has no inverse")
         return pow(a, -1, self.r)
 
     # --- Montgomery representation (R = 2^256) --------------------------------
     def to_mont(self, x: int) -> int:
+        """Montgomery form x * 2^256 mod r (the representation the paper's
+        FF_mul works on, Section IV-B)."""
         return (x * self.R) % self.r
 
     def from_mont(self, X: int) -> int:
+        """Canonical value X * 2^-256 mod r of a Montgomery-form X."""
         return (X * self.Rinv) % self.r
 
     def mont_mul(self, X: int, Y: int) -> int:

@@ -35,6 +35,9 @@ from workloads import ints_to_limbs, limbs_to_ints
 
 
 def bit_reverse(i: int, bits: int) -> int:
+    """The index permutation of the radix-2 algorithm (Section II-B, Fig. 3(b):
+    elements are reordered between stages; here i with its `bits` low bits
+    reversed)."""
     out = 0
     for _ in range(bits):
         out = (out << 1) | (i & 1)
@@ -43,13 +46,15 @@ def bit_reverse(i: int, bits: int) -> int:
 
 
 def dft(a: list[int], w: int, r: int) -> list[int]:
-    """The definition, O(n^2): A_k = sum_j a_j w^(j k) mod r."""
+    """The definition (Section II-B, with the index typo read as a_j), O(n^2):
+    A_k = sum_j a_j w^(j k) mod r."""
     n = len(a)
     return [sum(a[j] * pow(w, j * k, r) for j in range(n)) % r for k in range(n)]
 
 
 def eval_poly(a: list[int], x: int, r: int) -> int:
-    """sum_j a_j x^j mod r by Horner's rule."""
+    """sum_j a_j x^j mod r by Horner's rule: the coefficient vector read as a
+    polynomial (Section II-B: the transform evaluates it at the powers of w)."""
     acc = 0
     for coef in reversed(a):
         acc = (acc * x + coef) % r
@@ -57,7 +62,7 @@ def eval_poly(a: list[int], x: int, r: int) -> int:
 
 
 def dft_at(a: list[int], w: int, k: int, r: int) -> int:
-    """One output of the definition: A_k = a(w^k)."""
+    """One output of the definition (Section II-B): A_k = a(w^k)."""
     return eval_poly(a, pow(w, k, r), r)
 
 
@@ -91,7 +96,13 @@ def ntt_radix2(a: list[int], w: int, r: int) -> list[int]:
 
 def ntt(F: fld.Field, a: list[int], inverse: bool = False, shift: int | None = None,
         use_dft: bool = False) -> list[int]:
-    """Forward / inverse / coset transform of canonical values (length 2^L)."""
+    """Forward / inverse / coset transform of canonical values (length 2^L).
+
+    Forward: the definition of Section II-B.  Inverse: w^-1 and the factor
+    n^-1 (Section II-B treats the inverse as the same computation).  Coset
+    (the Groth16 step of Fig. 2): forward multiplies a_j by shift^j first,
+    inverse multiplies output j by shift^-j after.
+    """
     n = len(a)
     L = n.bit_length() - 1
     r = F.r
@@ -162,10 +173,13 @@ def four_step(F: fld.Field, a: list[int], n1: int, n2: int) -> list[int]:
 # --- Montgomery limb wrappers (the library's boundary layout) -----------------
 
 def from_mont_limbs(F: fld.Field, X: np.ndarray) -> list[int]:
+    """8 x 32-bit limbs (Section II: word-sized limbs) in Montgomery form ->
+    canonical integers."""
     return [F.from_mont(v) for v in limbs_to_ints(X)]
 
 
 def to_mont_limbs(F: fld.Field, x: list[int]) -> np.ndarray:
+    """Canonical integers -> Montgomery-form 8 x 32-bit limbs (Section II)."""
     return ints_to_limbs([F.to_mont(v) for v in x])
 
 
@@ -180,6 +194,7 @@ def ntt_mont(F, X: np.ndarray, inverse: bool = False, shift_mont: int | None = N
 
 
 def groth16_h_mont(F, A: np.ndarray, B: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """groth16_h (Fig. 2 and Section IV-A) on Montgomery-form limbs."""
     F = fld.get(F)
     a, b, c = (from_mont_limbs(F, v) for v in (A, B, C))
     return to_mont_limbs(F, groth16_h(F, a, b, c))
