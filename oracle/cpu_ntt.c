@@ -205,7 +205,8 @@ static void store(uint32_t *dst, const u64 v[4]) {
     }
 }
 
-/* omega_n (or its inverse) for n = 2^log_n, Montgomery form */
+/* omega_n (or its inverse) for n = 2^log_n, Montgomery form: the primitive
+ * n-th root the transform of Section II-B needs, w_max^(2^(s - log_n)) */
 static void root_of_unity(u64 out[4], const field_t *F, int log_n, int inverse) {
     u64 w[4];
     memcpy(w, F->wmax, sizeof w);
@@ -327,7 +328,9 @@ static void scale_powers(const field_t *F, u64 (*x)[4], u64 n, const u64 s[4], c
     parallel_for(threads, n, do_scale, &S);
 }
 
-/* transform in the Montgomery domain, natural order in and out */
+/* transform in the Montgomery domain, natural order in and out: radix-2
+ * decimation in time (Section II-B, Fig. 3(b)), with the inverse's n^-1 and
+ * the coset scales (Fig. 2) applied as separate passes */
 static int ntt_core(const field_t *F, int log_n, int inverse, const u64 *shift,
                     const u64 (*in)[4], u64 (*out)[4], int threads) {
     u64 n = (u64)1 << log_n;
@@ -399,12 +402,14 @@ int zo_threads_default(void) {
     return c > 0 ? (int)c : 1;
 }
 
+/* 2-adicity s of r - 1: the largest transform is 2^s (Section II-B) */
 int zo_two_adicity(int field) {
     if (field < 0 || field >= NFIELDS) return -1;
     fields_init();
     return FIELDS[field].s;
 }
 
+/* the primitive 2^log_n-th root (or its inverse), Montgomery form (Section II-B) */
 int zo_root(int field, int log_n, int inverse, uint32_t *out) {
     if (field < 0 || field >= NFIELDS) return 1;
     fields_init();
@@ -415,6 +420,7 @@ int zo_root(int field, int log_n, int inverse, uint32_t *out) {
     return 0;
 }
 
+/* Montgomery product a b 2^-256 mod r (FF_mul, Section IV-B) */
 int zo_mont_mul(int field, const uint32_t *a, const uint32_t *b, uint32_t *out) {
     if (field < 0 || field >= NFIELDS) return 1;
     fields_init();
@@ -426,6 +432,8 @@ int zo_mont_mul(int field, const uint32_t *a, const uint32_t *b, uint32_t *out) 
     return 0;
 }
 
+/* forward / inverse / coset transform of n = 2^log_n Montgomery-form elements
+ * (Section II-B; coset and inverse readings as in the file header) */
 int zo_ntt(int field, int log_n, int inverse, const uint32_t *shift_mont,
            const uint32_t *in, uint32_t *out, int threads) {
     if (check_args(field, log_n)) return 1;
@@ -441,7 +449,8 @@ int zo_ntt(int field, int log_n, int inverse, const uint32_t *shift_mont,
     return rc;
 }
 
-/* out = sum_j c_j x^j (Horner), all Montgomery form */
+/* out = sum_j c_j x^j (Horner), all Montgomery form: one output A_k of the
+ * Section II-B definition when x = w^k */
 int zo_eval(int field, uint64_t n, const uint32_t *coeffs, const uint32_t *x_mont, uint32_t *out) {
     if (field < 0 || field >= NFIELDS) return 1;
     fields_init();
@@ -469,6 +478,7 @@ static void do_pointwise(void *p, u64 lo, u64 hi) {
     }
 }
 
+/* the Groth16 H sequence (Fig. 2, Section IV-A) */
 int zo_groth16_h(int field, int log_n, const uint32_t *a, const uint32_t *b,
                  const uint32_t *c, uint32_t *h, int threads) {
     if (check_args(field, log_n)) return 1;
