@@ -82,7 +82,8 @@ typedef struct {
 } zkntt_plan_options;
 
 /*
- * Create a plan for one transform size/direction on the current CUDA device.
+ * Create a plan for one transform size/direction on the current CUDA device
+ * (the transform of Section II-B; the coset form of Fig. 2).
  *   out          receives the plan handle (not written on failure)
  *   field        ZKNTT_BLS12_381_FR, ZKNTT_BN254_FR or ZKNTT_BLS12_377_FR
  *   log_n        1 .. 28 for every field (device-memory bound; the fields'
@@ -98,38 +99,45 @@ typedef struct {
 zkntt_status zkntt_plan_create(zkntt_plan *out, zkntt_field field, int log_n, zkntt_dir dir,
                                const uint32_t *coset_shift);
 
-/* As zkntt_plan_create, with planner overrides (opts may be NULL). */
+/* As zkntt_plan_create, with planner overrides (opts may be NULL): the schedule
+ * parameters the paper asks to tune at run time (Section V-A). */
 zkntt_status zkntt_plan_create_ex(zkntt_plan *out, zkntt_field field, int log_n, zkntt_dir dir,
                                   const uint32_t *coset_shift, const zkntt_plan_options *opts);
 
-/* Free the plan's device tables.  The caller must ensure no work using the
- * plan is still in flight.  NULL is accepted. */
+/* Free the plan's device tables (resource management; the paper has no
+ * counterpart).  The caller must ensure no work using the plan is still in
+ * flight.  NULL is accepted. */
 zkntt_status zkntt_plan_destroy(zkntt_plan plan);
 
 /* Size in bytes of the scratch vector an execution of this plan needs
- * (0 for single-pass sizes, else n * 32). */
+ * (0 for single-pass sizes, else n * 32).  No counterpart in the paper. */
 zkntt_status zkntt_plan_scratch_bytes(zkntt_plan plan, size_t *bytes);
 
 /* Describe the plan: number of passes, digit bits per pass, twiddle mode and
- * the bytes of device tables it holds (any pointer may be NULL). */
+ * the bytes of device tables it holds (any pointer may be NULL).  No
+ * counterpart in the paper. */
 zkntt_status zkntt_plan_describe(zkntt_plan plan, int *num_passes, int digit_bits[4],
                                  int *twiddle_mode, size_t *table_bytes);
 
 /*
- * Run one transform: d_out = T(d_in), n = 2^log_n elements each.
+ * Run one transform: d_out = T(d_in), n = 2^log_n elements each (Section
+ * II-B: A_k = sum_j a_j w^(jk); inverse and coset as described above).
  * d_in == d_out (in place) is allowed; partial overlap is EINVAL.  Scratch for
  * multi-pass sizes comes from the device's stream-ordered memory pool
  * (cudaMallocAsync on `stream`, released on `stream`).
  */
 zkntt_status zkntt_execute(zkntt_plan plan, const void *d_in, void *d_out, void *stream);
 
-/* As zkntt_execute with caller-owned scratch (at least zkntt_plan_scratch_bytes
- * bytes, 32-byte aligned, not overlapping d_in/d_out); allocates nothing. */
+/* As zkntt_execute (Section II-B) with caller-owned scratch (at least
+ * zkntt_plan_scratch_bytes bytes, 32-byte aligned, not overlapping d_in/d_out);
+ * allocates nothing. */
 zkntt_status zkntt_execute_scratch(zkntt_plan plan, const void *d_in, void *d_out,
                                    void *d_scratch, size_t scratch_bytes, void *stream);
 
 /*
- * End-to-end form for callers holding the data in HOST memory: copies h_in
+ * End-to-end form for callers holding the data in HOST memory (the paper
+ * attributes part of existing libraries' NTT time to host-device transfers,
+ * Section IV-A; this form includes them): copies h_in
  * (n elements) to the device, runs the transform and copies the result to
  * h_out, all ordered on `stream` (device buffers come from the stream-ordered
  * pool and are released on the stream).  Returns once enqueued; h_out is valid
@@ -170,7 +178,9 @@ zkntt_status zkntt_execute_noalloc(zkntt_plan plan, const void *d_in, void *d_ou
 
 /*
  * Run `count` independent transforms (each with its own plan; sizes, fields and
- * directions may differ) as ONE persistent kernel launch.  Work items (job,
+ * directions may differ) as ONE persistent kernel launch per field (the paper
+ * finds provers issuing each transform as several short launches, Section
+ * IV-A, and calls for batching and run-time tuning, Section V-A).  Work items (job,
  * pass, tile) are pulled from a device queue; a job's pass starts once all its
  * previous pass's tiles are done (bounded spin; on expiry the launch sets an
  * error word and returns, reported as ETIMEOUT).  ptrs[i] gives job i's
@@ -181,7 +191,9 @@ zkntt_status zkntt_execute_batch(const zkntt_plan *plans, const zkntt_io *ptrs, 
                                  void *stream);
 
 /*
- * As zkntt_execute_batch, for serving: transforms are scheduled shortest
+ * As zkntt_execute_batch, for serving (transform sizes vary by application,
+ * Section IV-A; the serving loop itself has no counterpart in the paper):
+ * transforms are scheduled shortest
  * first, each one's passes back to back, and when transform i has completed on
  * the device the launch stores `epoch` into d_flags[i] with a system-scope
  * release, so a host thread polling host-mapped memory (zkntt_flags_create)
@@ -193,12 +205,13 @@ zkntt_status zkntt_execute_batch_signal(const zkntt_plan *plans, const zkntt_io 
                                         uint32_t *d_flags, uint32_t epoch, void *stream);
 
 /* Pinned host words that the device can write (zero-copy): host_view for
- * polling, device_view for zkntt_execute_batch_signal.  Zero-initialised. */
+ * polling, device_view for zkntt_execute_batch_signal.  Zero-initialised.
+ * Support for the serving form; no counterpart in the paper. */
 zkntt_status zkntt_flags_create(int count, uint32_t **host_view, uint32_t **device_view);
 zkntt_status zkntt_flags_destroy(uint32_t *host_view);
 
 /*
- * Groth16 H polynomial (Fig. 2; Section IV-A: seven NTT operations):
+ * Groth16 H polynomial (Fig. 2; Section IV-A counts seven transforms):
  *   a' = iNTT(a), b' = iNTT(b), c' = iNTT(c);
  *   A = cosetNTT_g(a'), B = cosetNTT_g(b'), C = cosetNTT_g(c');
  *   H_i = (A_i B_i - C_i) * (g^n - 1)^-1     (Z(x) = x^n - 1 on the coset g*w^i)
@@ -214,7 +227,8 @@ zkntt_status zkntt_groth16_h(zkntt_field field, int log_n, const void *d_a, cons
                              void *stream);
 
 /*
- * The fused Groth16 H sequence captured once into a CUDA graph: the capture
+ * The fused Groth16 H sequence (Fig. 2) captured once into a CUDA graph (the
+ * launch-overhead reduction Section V-A points to): the capture
  * records the persistent launch and its stream-ordered scratch allocations
  * for these exact buffers; each zkntt_graph_launch replays it on `stream`
  * with no host-side work per transform.  `stream` must be a created stream
@@ -230,30 +244,36 @@ zkntt_status zkntt_groth16_graph_create(zkntt_graph *out, zkntt_field field, int
 zkntt_status zkntt_graph_launch(zkntt_graph graph, void *stream);
 zkntt_status zkntt_graph_destroy(zkntt_graph graph);
 
-/* Static text for a status code. */
+/* Static text for a status code (error reporting; no counterpart in the paper). */
 const char *zkntt_status_str(zkntt_status status);
 
-/* The last CUDA error code this library saw on the calling thread (0 = none). */
+/* The last CUDA error code this library saw on the calling thread (0 = none).
+ * Error reporting; no counterpart in the paper. */
 zkntt_status zkntt_last_cuda_error(int *err);
 
 /* Wait for `stream` and report any device-side error word (ETIMEOUT) or CUDA
- * error raised by work this library enqueued on it. */
+ * error raised by work this library enqueued on it.  Error reporting; no
+ * counterpart in the paper. */
 zkntt_status zkntt_sync_status(void *stream);
 
-/* Fault-injection self-test of the persistent kernel's bounded wait: launches
+/* Fault-injection self-test of the persistent kernel's bounded wait (failure
+ * detection; no counterpart in the paper): launches
  * it with a single work item whose dependency can never be met (injected on
  * the host) and a device-side wait limit of timeout_ms, then returns what
  * zkntt_sync_status reports -- ZKNTT_ETIMEOUT when the bound works.  No GPU
  * fault is involved; the context stays usable. */
 zkntt_status zkntt_selftest_timeout(int timeout_ms, void *stream);
 
-/* Field information: modulus and Montgomery form of the generator, 8 limbs
- * each (host memory, either may be NULL), and the 2-adicity. */
+/* Field information (the prime fields of Section II; the generator is this
+ * library's reading, the paper prints none): modulus and Montgomery form of the
+ * generator, 8 limbs each (host memory, either may be NULL), and the
+ * 2-adicity. */
 zkntt_status zkntt_field_info(zkntt_field field, uint32_t modulus[8], uint32_t generator_mont[8],
                               int *two_adicity);
 
-/* Elementwise field operations on device vectors of n elements (test and
- * calibration entry points for the butterfly arithmetic):
+/* Elementwise field operations on device vectors of n elements (FF_mul,
+ * FF_add and FF_sub of Section IV-B; test and calibration entry points for
+ * the butterfly arithmetic):
  *   op 0: c = a * b (Montgomery product a b 2^-256 mod r, canonical; a must be
  *         canonical, b may be any 256-bit value)
  *   op 1: c = a + b mod r      op 2: c = a - b mod r
@@ -264,8 +284,8 @@ zkntt_status zkntt_field_info(zkntt_field field, uint32_t modulus[8], uint32_t g
 zkntt_status zkntt_field_op(zkntt_field field, int op, const void *d_a, const void *d_b, void *d_c,
                             size_t n, void *stream);
 
-/* Groth16 pointwise step on its own: d_h_i = (a_i b_i - c_i) * z, z given as
- * 8 Montgomery limbs in host memory. */
+/* Groth16 pointwise step on its own (the (A B - C) / Z step of Fig. 2):
+ * d_h_i = (a_i b_i - c_i) * z, z given as 8 Montgomery limbs in host memory. */
 zkntt_status zkntt_pointwise(zkntt_field field, const void *d_a, const void *d_b, const void *d_c,
                              const uint32_t *z_mont, void *d_h, size_t n, void *stream);
 
@@ -294,7 +314,8 @@ zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_can
                         zkntt_tune_result *best);
 
 /*
- * Integer-pipe calibration: runs `iters` Montgomery products per thread on a
+ * Integer-pipe calibration (Sections IV-B and IV-C find FF_mul bound by the
+ * 32-bit integer pipe): runs `iters` Montgomery products per thread on a
  * grid of `blocks` x `threads` (register-resident, no memory traffic inside
  * the loop) and writes one checksum word per thread to d_sink.  Used to
  * measure the sustained 32-bit multiply-add rate that bounds the transform.
