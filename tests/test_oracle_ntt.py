@@ -262,3 +262,54 @@ def test_groth16_pins_catch_planted_mistakes():
         lhs = ref.eval_poly(h, x, r) * (pow(x, n, r) - 1) % r
         rhs = (ref.eval_poly(ap, x, r) * ref.eval_poly(bp, x, r) - ref.eval_poly(cp, x, r)) % r
         assert h[n - 1] != 0 or lhs != rhs, bad.__name__
+
+
+@pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
+@pytest.mark.parametrize("n", [8, 64, 256])
+def test_shift_theorem(F, n):
+    """A cyclic shift of the input by s multiplies output k by w^(s k) (a
+    property of the DFT that pins the sign of the exponent and the index
+    convention independently of the oracle's own formulas)."""
+    r = F.r
+    rng = random.Random(90 + n)
+    a = [rng.randrange(r) for _ in range(n)]
+    w = F.root(n.bit_length() - 1)
+    A = ref.ntt(F, a)
+    for s in (1, 3, n // 2, n - 1):
+        shifted = [a[(j - s) % n] for j in range(n)]
+        B = ref.ntt(F, shifted)
+        assert B == [A[k] * pow(w, s * k, r) % r for k in range(n)], s
+
+
+@pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
+def test_linearity(F):
+    """NTT(alpha a + beta b) = alpha NTT(a) + beta NTT(b), forward, inverse and
+    coset (the coset and inverse scales are linear too)."""
+    r = F.r
+    rng = random.Random(91)
+    n = 128
+    a = [rng.randrange(r) for _ in range(n)]
+    b = [rng.randrange(r) for _ in range(n)]
+    alpha, beta = rng.randrange(r), rng.randrange(r)
+    mix = [(alpha * x + beta * y) % r for x, y in zip(a, b)]
+    for kw in ({}, {"inverse": True}, {"shift": F.g}, {"inverse": True, "shift": F.g}):
+        A, B, M = ref.ntt(F, a, **kw), ref.ntt(F, b, **kw), ref.ntt(F, mix, **kw)
+        assert M == [(alpha * x + beta * y) % r for x, y in zip(A, B)], kw
+
+
+@pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
+def test_c_oracle_shift_theorem_at_larger_size(F):
+    """The shift theorem on the C oracle at 2^14 (sizes the Python oracle is
+    slow for): output k of the shifted input equals output k times w^(s k)."""
+    from oracle import cpu
+    L = 14
+    n = 1 << L
+    X = uniform_elements(F.r, n, 92)
+    s = 12345
+    Xs = np.roll(X, s, axis=0)           # Xs[j] = X[j - s]
+    A = limbs_to_ints(cpu.ntt(F, X))
+    B = limbs_to_ints(cpu.ntt(F, Xs))
+    w = F.root(L)
+    for k in (0, 1, 7, n // 3, n - 1):
+        # Montgomery forms: B_k = A_k * w^(s k)  <=>  B~_k = A~_k * w^(s k) (plain factor)
+        assert B[k] == A[k] * pow(w, s * k, F.r) % F.r, k
