@@ -66,3 +66,24 @@ def test_two_rank_gloo_sharding_and_reductions():
     assert sorted(g0[0] + g0[1]) == list(range(64))   # disjoint cover
     assert total0 == total1 == float(sum(1 << j.log_n for j in jobs))
     assert slow0 == slow1 == 3.0
+
+
+def test_shard_properties_over_generated_inputs():
+    """For generated unit lists and world sizes: the shards partition the
+    units, every rank computes the same assignment, and the load imbalance is
+    at most the largest unit (the greedy largest-first bound)."""
+    hypothesis = pytest.importorskip("hypothesis")
+    from hypothesis import given, settings, strategies as st
+
+    @settings(max_examples=60, deadline=None)
+    @given(log_ns=st.lists(st.integers(1, 24), min_size=0, max_size=80), world=st.integers(1, 9))
+    def check(log_ns, world):
+        parts = shard_units(log_ns, world)
+        assert len(parts) == world
+        assert sorted(i for p in parts for i in p) == list(range(len(log_ns)))
+        assert parts == shard_units(list(log_ns), world)      # deterministic
+        if log_ns:
+            loads = [sum(unit_cost(log_ns[i]) for i in p) for p in parts]
+            assert max(loads) - min(loads) <= max(unit_cost(L) for L in log_ns)
+
+    check()
