@@ -220,9 +220,11 @@ def cpu_oracle_rate(field: str, log_n: int, budget_s: float, X=None):
     return (reps << log_n) / el / 1e6, threads, reps, el
 
 
-def host_link_gbs(torch, h_in, h_out, d_buf, reps: int = 3):
-    """Pinned host <-> device copy bandwidth (GB/s) for one vector, each
-    direction alone, timed with CUDA events on a side stream."""
+def host_link_gbs(torch, h_in, h_out, d_buf, d_buf2, reps: int = 3):
+    """Pinned host <-> device copy bandwidth (GB/s) for one vector: each
+    direction alone, then both at once on two streams (aggregate), timed with
+    CUDA events.  The two directions overlap only where the device has a copy
+    engine for each."""
     s = torch.cuda.Stream()
     out = []
     for direction in ("h2d", "d2h"):
@@ -239,6 +241,17 @@ def host_link_gbs(torch, h_in, h_out, d_buf, reps: int = 3):
             e1.record(s)
         e1.synchronize()
         out.append(round(reps * h_in.numel() * h_in.element_size() / (e0.elapsed_time(e1) / 1e3) / 1e9, 1))
+    s2 = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(s):
+        for _ in range(reps):
+            d_buf.copy_(h_in, non_blocking=True)
+    with torch.cuda.stream(s2):
+        for _ in range(reps):
+            h_out.copy_(d_buf2, non_blocking=True)
+    torch.cuda.synchronize()
+    out.append(round(2 * reps * h_in.numel() * h_in.element_size() / (time.perf_counter() - t0) / 1e9, 1))
     return out
 
 
@@ -572,7 +585,7 @@ def run_ours(args, world, rank, local):
     ms_e2e = max_over_ranks(world, e2e_run(e2e_steps))
     ok = all(bool(np.array_equal(yh.numpy().view(np.uint32), y.cpu().numpy().view(np.uint32)))
              for yh in yhs)
-    link = host_link_gbs(torch, xh, yhs[0], x)
+    link = host_link_gbs(torch, xh, yhs[0], x, y)
 
     passes = desc["passes"]
     avg_launch_s = ms_total / 1e3 / (args.steps * passes)
@@ -615,7 +628,8 @@ def run_ours(args, world, rank, local):
                 # pinned-copy bandwidth of this machine, one direction at a time: the
                 # copies of a step are hidden behind its transform only while
                 # 32n bytes each way take less than the transform
-                "link_h2d_gbs": link[0], "link_d2h_gbs": link[1]},
+                "link_h2d_gbs": link[0], "link_d2h_gbs": link[1],
+                "link_both_directions_gbs": link[2]},
         "gpu_launches": args.steps * passes,
         "clocks": clk,
     }
