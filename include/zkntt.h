@@ -146,6 +146,14 @@ zkntt_status zkntt_execute_scratch(zkntt_plan plan, const void *d_in, void *d_ou
  */
 zkntt_status zkntt_execute_host(zkntt_plan plan, const void *h_in, void *h_out, void *stream);
 
+/* As zkntt_execute_host with a caller-owned device work buffer instead of the
+ * pool: d_work holds the vector and the plan's scratch, so work_bytes must be
+ * at least n * 32 + zkntt_plan_scratch_bytes (32-byte aligned); nothing is
+ * allocated in the call.  For callers that stream many transforms through
+ * host memory (one work buffer per stream in flight). */
+zkntt_status zkntt_execute_host_buffered(zkntt_plan plan, const void *h_in, void *h_out,
+                                         void *d_work, size_t work_bytes, void *stream);
+
 /* Largest scratch zkntt_execute_noalloc can use: 32 MiB, i.e. transforms of up
  * to 2^20 elements. */
 #define ZKNTT_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)

@@ -142,6 +142,25 @@ class Plan:
                                            _stream_handle(stream)), "zkntt_execute_host")
         return out_host
 
+    def work_bytes(self) -> int:
+        """Device bytes execute_host_buffered needs: the vector plus scratch."""
+        return 32 * self.n + self.scratch_bytes()
+
+    def execute_host_buffered(self, x_host: torch.Tensor, out_host: torch.Tensor,
+                              work: torch.Tensor, stream=None):
+        """As execute_host with a caller-owned device work buffer (at least
+        work_bytes() bytes): no allocation inside the call."""
+        self._check_vec(x_host)
+        self._check_vec(out_host)
+        if x_host.is_cuda or out_host.is_cuda or not work.is_cuda:
+            raise ValueError("host tensors in and out, a device work buffer")
+        nbytes = work.numel() * work.element_size()
+        N.check(N.lib().zkntt_execute_host_buffered(self.handle, ctypes.c_void_p(x_host.data_ptr()),
+                                                    ctypes.c_void_p(out_host.data_ptr()),
+                                                    _ptr(work), nbytes, _stream_handle(stream)),
+                "zkntt_execute_host_buffered")
+        return out_host
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             N.lib().zkntt_plan_destroy(self._h)

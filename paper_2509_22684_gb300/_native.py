@@ -57,6 +57,7 @@ SIGNATURES = {
     "zkntt_execute": [_vp, _vp, _vp, _vp],
     "zkntt_execute_scratch": [_vp, _vp, _vp, _vp, _sz, _vp],
     "zkntt_execute_host": [_vp, _vp, _vp, _vp],
+    "zkntt_execute_host_buffered": [_vp, _vp, _vp, _vp, _sz, _vp],
     "zkntt_execute_noalloc": [_vp, _vp, _vp, _vp],
     "zkntt_execute_batch": [ctypes.POINTER(_vp), ctypes.POINTER(IO), _i, _vp],
     "zkntt_execute_batch_signal": [ctypes.POINTER(_vp), ctypes.POINTER(IO), _i, _vp, ctypes.c_uint32, _vp],

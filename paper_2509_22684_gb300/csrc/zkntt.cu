@@ -1018,6 +1018,20 @@ zkntt_status zkntt_execute_host(zkntt_plan plan, const void *h_in, void *h_out, 
     return st != ZKNTT_OK ? st : st2;
 }
 
+zkntt_status zkntt_execute_host_buffered(zkntt_plan plan, const void *h_in, void *h_out,
+                                         void *d_work, size_t work_bytes, void *stream) {
+    if (!plan || !h_in || !h_out || bad_ptr(d_work)) return ZKNTT_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = size_t(32) << plan->log_n;
+    const size_t need = scratch_bytes_of(plan);
+    if (work_bytes < bytes + need) return ZKNTT_EINVAL;
+    char *buf = static_cast<char *>(d_work);
+    zkntt_status st = from_cuda(cudaMemcpyAsync(buf, h_in, bytes, cudaMemcpyHostToDevice, s));
+    if (st == ZKNTT_OK) st = run_passes(plan, buf, buf, need ? buf + bytes : nullptr, s);
+    if (st == ZKNTT_OK) st = from_cuda(cudaMemcpyAsync(h_out, buf, bytes, cudaMemcpyDeviceToHost, s));
+    return st;
+}
+
 zkntt_status zkntt_execute_noalloc(zkntt_plan plan, const void *d_in, void *d_out, void *stream) {
     if (!plan || bad_ptr(d_in) || bad_ptr(d_out)) return ZKNTT_EINVAL;
     const size_t bytes = size_t(32) << plan->log_n;

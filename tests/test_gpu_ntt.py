@@ -204,3 +204,26 @@ def test_tuner_picks_a_schedule_that_stays_exact(tmp_path, monkeypatch):
         assert p.describe()["digits"] == best["digits"]
         got = to_host(p.execute(x))
     assert np.array_equal(got, cpu.ntt(F, X, inverse=True))
+
+
+@pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
+def test_execute_host_buffered_matches_device_execution(F):
+    """Host buffers in and out with a caller-owned device work buffer: the
+    result equals the device-resident execution; a too-small buffer is
+    rejected before anything is enqueued."""
+    import torch
+    import paper_2509_22684_gb300 as zk
+    from paper_2509_22684_gb300 import ZkNttError
+    L = 18
+    X, x = rand_dev(F, L, 1818)
+    with _plan(F, L, "coset_intt") as p:
+        want = to_host(p.execute(x))
+        xh = torch.from_numpy(X.view(np.int32)).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        work = torch.empty(p.work_bytes() // 4, dtype=torch.int32, device="cuda")
+        s = torch.cuda.Stream()
+        p.execute_host_buffered(xh, yh, work, stream=s)
+        s.synchronize()
+        assert np.array_equal(yh.numpy().view(np.uint32).reshape(-1, 8), want)
+        with pytest.raises(ZkNttError):
+            p.execute_host_buffered(xh, yh, work[:8 * (1 << L)], stream=s)
