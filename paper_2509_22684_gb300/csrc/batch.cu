@@ -1,4 +1,4 @@
-// batch.cu -- the persistent batch kernel (both fields, every digit size).
+// batch.cu -- the persistent batch kernel (one instantiation per field, every digit size).
 #include "batch.cuh"
 #include "kernels.h"
 

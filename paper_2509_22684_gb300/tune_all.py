@@ -1,6 +1,6 @@
 """Tune transform schedules for every size on the current GPU.
 
-Runs the library's autotuner (zkntt_tune) for both fields, both directions and
+Runs the library's autotuner (zkntt_tune) for every field (or --fields), both directions and
 log_n in a range, and writes the winners as JSON lines to --out.  Copying that
 file to ``zkntt_tuned.jsonl`` next to ``libzkntt.so`` makes every plan created
 on a GPU with the same name use the tuned schedules.
