@@ -217,15 +217,29 @@ extern "C" zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, 
         bool ok = true;
         for (int w = 0; w < 2 && ok; w++)
             ok = zkntt_execute_scratch(plan, in, out, scr, bytes, s) == ZKNTT_OK;
-        std::vector<float> t;
-        for (int r = 0; r < 5 && ok; r++) {
+        // each sample times `reps` back-to-back executions (at least ~1 ms of
+        // work), so small transforms are timed at their throughput rather than
+        // at one launch's latency and the events' resolution
+        int reps = 1;
+        if (ok) {
             cudaEventRecord(e0, s);
             ok = zkntt_execute_scratch(plan, in, out, scr, bytes, s) == ZKNTT_OK;
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
+            float one = 0;
+            cudaEventElapsedTime(&one, e0, e1);
+            reps = std::max(1, std::min(200, int(1.0f / std::max(one, 1e-3f)) + 1));
+        }
+        std::vector<float> t;
+        for (int r = 0; r < 5 && ok; r++) {
+            cudaEventRecord(e0, s);
+            for (int k = 0; k < reps && ok; k++)
+                ok = zkntt_execute_scratch(plan, in, out, scr, bytes, s) == ZKNTT_OK;
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
-            t.push_back(ms);
+            t.push_back(ms / float(reps));
         }
         zkntt_plan_destroy(plan);
         if (!ok || t.empty()) continue;
