@@ -267,6 +267,23 @@ def timed(fn, stream, steps: int) -> float:
     return e0.elapsed_time(e1)
 
 
+def measured_imad_peak(zk, torch, sms: int, stream) -> dict:
+    """The 32-bit multiply-add rate of this GPU, measured in this process with
+    the library's calibration kernel (zkntt_imadbench): eight independent
+    register chains per thread, 2048 threads per SM; best of three timed
+    launches after a warm-up, for mad.lo.u32 and for mad.wide.u32."""
+    blocks, threads, iters = sms * 8, 256, 1 << 16
+    sink = torch.empty(blocks * threads, dtype=torch.int32, device="cuda")
+    out = {}
+    for mode, name in ((0, "mad_lo_per_s"), (1, "mad_wide_per_s")):
+        zk.imadbench(mode, blocks, threads, iters // 16, sink, stream=stream)
+        best = min(timed(lambda: zk.imadbench(mode, blocks, threads, iters, sink, stream=stream),
+                         stream, 1) for _ in range(3))
+        out[name] = blocks * threads * 8 * iters / (best / 1e3)
+    out["config"] = f"{blocks} blocks x {threads} threads x 8 chains x {iters} steps"
+    return out
+
+
 def extras(zk, torch, field: str, stream, peak_imad: float, hbm_gbs: float) -> dict:
     """Other sizes, twiddle modes, and batched vs plain (rank 0, short runs)."""
     import numpy as np
@@ -417,7 +434,9 @@ def serve_bench(zk, torch, field: str, n_requests: int, loads, solo_log_n=None) 
         rate = load / mean_svc
         trace = poisson_trace(5000, n_requests, rate, 12, 24)
         mk = lambda: [Request(i, q.arrival_s, field, q.log_n, q.kind) for i, q in enumerate(trace)]
-        eng = Engine(ex, budget_bytes=int(torch.cuda.mem_get_info()[0] * 0.5), streams=2,
+        # admission: live free device memory less a reserve (the executor's
+        # headroom), within the device's total as the outer budget
+        eng = Engine(ex, budget_bytes=int(torch.cuda.mem_get_info()[1]), streams=2,
                      max_batch_jobs=64, solo_log_n=solo_log_n)
         _, st = eng.run(mk())
         _, ser = serve_serial(mk(), run_one)
@@ -589,6 +608,7 @@ def run_ours(args, world, rank, local):
              for yh in yhs)
     link = host_link_gbs(torch, xh, yhs[0], x, y)
 
+    imad = measured_imad_peak(zk, torch, sms, stream)
     passes = desc["passes"]
     avg_launch_s = ms_total / 1e3 / (args.steps * passes)
     alg_imad_per_launch = butterfly_mults(L) * IMAD_PER_MUL / passes
@@ -617,6 +637,12 @@ def run_ours(args, world, rank, local):
         "roofline": {"bound": "alu", "achieved": round(achieved / 1e12, 3),
                      "peak": round(peak_imad / 1e12, 3), "unit": "TIMAD/s",
                      "frac": round(achieved / peak_imad, 4),
+                     # against the multiply-add rate measured in this run
+                     # (independent mad.lo.u32 chains; zkntt_imadbench)
+                     "peak_measured": round(imad["mad_lo_per_s"] / 1e12, 3),
+                     "frac_measured": round(achieved / imad["mad_lo_per_s"], 4),
+                     "wide_rate_measured": round(imad["mad_wide_per_s"] / 1e12, 3),
+                     "peak_measured_config": imad["config"],
                      "traffic": traffic,
                      "kernel": "ntt_pass_kernel (all passes of one transform)",
                      "peak_source": f"derived: {sms} SMs x {IMAD_LANES_PER_SM_CLK} IMAD/clk x {sm_max_mhz:.0f} MHz",
@@ -708,7 +734,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-loads", default="0.5,0.8,0.95",
                     help="offered loads, as fractions of the serial capacity")
     ap.add_argument("--serve-solo-log-n", type=int, default=20,

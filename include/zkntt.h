@@ -23,9 +23,14 @@
  * execute call is stream-ordered and asynchronous: it returns once the work is
  * enqueued.  Errors the host can see (bad arguments, launch failures) are
  * returned at once; a device-side timeout of the persistent batch kernel is
- * returned by zkntt_sync_status() or by the next zkntt_execute_batch() on the
- * same context.  Plans are immutable after creation: one plan may be executed
- * from several host threads and streams at once.
+ * returned by zkntt_sync_status() on the stream the launch ran on (each stream
+ * has its own error word).  Plans are immutable after creation: one plan may be
+ * executed from several host threads and streams at once, but only while the
+ * device it was created on is current: every execute entry point returns
+ * ZKNTT_EINVAL, before enqueuing anything, when another device is current.
+ * Stream-ordered scratch comes from a memory pool private to this library (one
+ * per device; freed blocks stay in it for reuse); the device's default pool is
+ * not touched.
  */
 #ifndef ZKNTT_H
 #define ZKNTT_H
@@ -122,9 +127,10 @@ zkntt_status zkntt_plan_describe(zkntt_plan plan, int *num_passes, int digit_bit
 /*
  * Run one transform: d_out = T(d_in), n = 2^log_n elements each (Section
  * II-B: A_k = sum_j a_j w^(jk); inverse and coset as described above).
- * d_in == d_out (in place) is allowed; partial overlap is EINVAL.  Scratch for
- * multi-pass sizes comes from the device's stream-ordered memory pool
- * (cudaMallocAsync on `stream`, released on `stream`).
+ * d_in == d_out (in place) is allowed; partial overlap is EINVAL; a plan of
+ * another device than the current one is EINVAL.  Scratch for multi-pass
+ * sizes comes from the library's stream-ordered pool (allocated on `stream`,
+ * released on `stream`).
  */
 zkntt_status zkntt_execute(zkntt_plan plan, const void *d_in, void *d_out, void *stream);
 
@@ -252,6 +258,14 @@ zkntt_status zkntt_groth16_graph_create(zkntt_graph *out, zkntt_field field, int
 zkntt_status zkntt_graph_launch(zkntt_graph graph, void *stream);
 zkntt_status zkntt_graph_destroy(zkntt_graph graph);
 
+/* The library's stream-ordered scratch pool on the current device (memory
+ * management; no counterpart in the paper): *reserved_bytes is the device
+ * memory the pool holds, *used_bytes the part handed out to executions in
+ * flight.  The difference is free for the library's next executions although
+ * cudaMemGetInfo counts it as used; a caller admitting work by free device
+ * memory (a serving loop) adds it back. */
+zkntt_status zkntt_pool_info(size_t *reserved_bytes, size_t *used_bytes);
+
 /* Static text for a status code (error reporting; no counterpart in the paper). */
 const char *zkntt_status_str(zkntt_status status);
 
@@ -260,8 +274,12 @@ const char *zkntt_status_str(zkntt_status status);
 zkntt_status zkntt_last_cuda_error(int *err);
 
 /* Wait for `stream` and report any device-side error word (ETIMEOUT) or CUDA
- * error raised by work this library enqueued on it.  Error reporting; no
- * counterpart in the paper. */
+ * error raised by work this library enqueued on it; the stream's error word is
+ * cleared once reported.  Each stream has its own word (the first 1023 streams
+ * that run a batch launch on a device; later ones share one more), so a
+ * timeout on one stream is not reported on another.  A captured launch
+ * (zkntt_groth16_graph_create) reports to the word of the stream it was
+ * captured on.  Error reporting; no counterpart in the paper. */
 zkntt_status zkntt_sync_status(void *stream);
 
 /* Fault-injection self-test of the persistent kernel's bounded wait (failure
@@ -271,6 +289,25 @@ zkntt_status zkntt_sync_status(void *stream);
  * zkntt_sync_status reports -- ZKNTT_ETIMEOUT when the bound works.  No GPU
  * fault is involved; the context stays usable. */
 zkntt_status zkntt_selftest_timeout(int timeout_ms, void *stream);
+
+/* The launch half of zkntt_selftest_timeout (failure detection; no counterpart
+ * in the paper): enqueues the same never-satisfied single-item launch with a
+ * wait limit of timeout_ms (1..10000, else ZKNTT_EINVAL) on `stream` and
+ * returns once enqueued.  When the wait gives up, the launch sets `stream`'s
+ * error word, so zkntt_sync_status(stream) returns ZKNTT_ETIMEOUT while the
+ * other streams' words stay clear. */
+zkntt_status zkntt_inject_timeout(int timeout_ms, void *stream);
+
+/* Self-test of the plan-device check (argument validation; no counterpart in
+ * the paper).  A plan's tables live on the device that was current when it was
+ * created, and every execute entry point returns ZKNTT_EINVAL, before enqueuing
+ * anything, when another device is current.  This creates a 16-element plan
+ * on the current device, marks a copy of it as belonging to another device,
+ * passes the copy to each of the execute entry points (zkntt_execute, _scratch,
+ * _host, _host_buffered, _noalloc, _batch, _batch_signal) with real 16-element
+ * buffers, and reports how many were called (*checked) and how many returned
+ * ZKNTT_EINVAL (*rejected).  Synchronous; frees everything it created. */
+zkntt_status zkntt_selftest_device_check(int *checked, int *rejected);
 
 /* Field information (the prime fields of Section II; the generator is this
  * library's reading, the paper prints none): modulus and Montgomery form of the
@@ -330,6 +367,20 @@ zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_can
  */
 zkntt_status zkntt_mulbench(zkntt_field field, int blocks, int threads, int iters, void *d_sink,
                             void *stream);
+
+/*
+ * Peak calibration of the 32-bit integer multiply-add (IMAD) rate, the
+ * denominator of the transform's roofline (Sections IV-B and IV-C find FF_mul
+ * bound by the INT32 pipe and weight IMAD in its integer roofline): a grid of
+ * `blocks` x `threads` (32..1024) runs `iters` steps of eight independent
+ * register-resident chains per thread, of mad.lo.u32 (mode 0: one 32-bit
+ * multiply-add) or mad.wide.u32 (mode 1: a 32 x 32 -> 64 multiply-add), and
+ * writes one checksum word per thread to d_sink.  8 * iters multiply-adds per
+ * thread; time it with CUDA events on `stream`.  mode outside 0..1 or bad
+ * sizes -> ZKNTT_EINVAL.
+ */
+zkntt_status zkntt_imadbench(int mode, int blocks, int threads, int iters, void *d_sink,
+                             void *stream);
 
 #ifdef __cplusplus
 }

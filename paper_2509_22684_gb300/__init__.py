@@ -17,7 +17,8 @@ from ._native import ZkNttError, FIELDS, TWIDDLE_MODES
 
 __all__ = ["Plan", "ZkNttError", "FIELDS", "execute_batch", "execute_batch_signal",
            "CompletionFlags", "groth16_h", "Groth16Graph", "field_info",
-           "field_op", "pointwise", "tune", "sync_status", "mulbench", "new_vector"]
+           "field_op", "pointwise", "tune", "sync_status", "mulbench", "imadbench", "pool_info",
+           "new_vector"]
 
 
 def _field_id(field) -> int:
@@ -325,6 +326,20 @@ def tune(field, log_n: int, inverse: bool = False, max_candidates: int = 24) -> 
 
 def sync_status(stream=None) -> None:
     N.check(N.lib().zkntt_sync_status(_stream_handle(stream)), "zkntt_sync_status")
+
+
+def pool_info() -> tuple[int, int]:
+    """(reserved, in use) bytes of the library's scratch pool on the current device."""
+    r, u = ctypes.c_size_t(), ctypes.c_size_t()
+    N.check(N.lib().zkntt_pool_info(ctypes.byref(r), ctypes.byref(u)), "zkntt_pool_info")
+    return r.value, u.value
+
+
+def imadbench(mode: int, blocks: int, threads: int, iters: int, sink: torch.Tensor, stream=None):
+    """Launch the multiply-add rate calibration (mode 0 mad.lo.u32, 1
+    mad.wide.u32): 8 * iters multiply-adds per thread."""
+    N.check(N.lib().zkntt_imadbench(int(mode), blocks, threads, iters, _ptr(sink),
+                                    _stream_handle(stream)), "zkntt_imadbench")
 
 
 def mulbench(field, blocks: int, threads: int, iters: int, sink: torch.Tensor, stream=None):

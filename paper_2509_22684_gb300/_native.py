@@ -71,11 +71,15 @@ SIGNATURES = {
     "zkntt_last_cuda_error": [ctypes.POINTER(_i)],
     "zkntt_sync_status": [_vp],
     "zkntt_selftest_timeout": [_i, _vp],
+    "zkntt_inject_timeout": [_i, _vp],
     "zkntt_field_info": [_i, _u32p, _u32p, ctypes.POINTER(_i)],
     "zkntt_field_op": [_i, _i, _vp, _vp, _vp, _sz, _vp],
     "zkntt_pointwise": [_i, _vp, _vp, _vp, _u32p, _vp, _sz, _vp],
     "zkntt_tune": [_i, _i, _i, _i, ctypes.POINTER(TuneResult)],
     "zkntt_mulbench": [_i, _i, _i, _i, _vp, _vp],
+    "zkntt_imadbench": [_i, _i, _i, _i, _vp, _vp],
+    "zkntt_selftest_device_check": [ctypes.POINTER(_i), ctypes.POINTER(_i)],
+    "zkntt_pool_info": [ctypes.POINTER(_sz), ctypes.POINTER(_sz)],
 }
 
 

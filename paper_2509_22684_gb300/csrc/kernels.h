@@ -26,5 +26,7 @@ constexpr int NUM_FIELDS = 3;
 // pass-kernel schedule variants, 1 .. NUM_VARIANTS (the plan's `ilp` option)
 constexpr int NUM_VARIANTS = 5;
 const void *batch_kernel_ptr(int field);
+// the 32-bit multiply-add rate calibration kernel (field-independent)
+const void *imadbench_kernel_ptr();
 
 }  // namespace zkntt

@@ -151,7 +151,53 @@ void splits(int L, int p, std::vector<std::vector<int>> &out) {
 
 using namespace zkntt;
 
-extern "C" zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_candidates,
+extern "C" // The tuning input: uniform field elements (SplitMix64 words, rejection-sampled
+// below r) rather than zeros, so the candidates are timed on the bit activity --
+// and hence the power draw and sustained clock -- of real data.  A block of
+// 2^16 elements is drawn on the host and repeated over the vector by
+// device-to-device copies.
+static zkntt_status fill_uniform(zkntt_field field, void *d, size_t n) {
+    uint32_t r[8];
+    int s = 0;
+    zkntt_status st = zkntt_field_info(field, r, nullptr, &s);
+    if (st != ZKNTT_OK) return st;
+    int top = 255;
+    while (top > 0 && !((r[top / 32] >> (top % 32)) & 1u)) top--;
+    const size_t blk = std::min<size_t>(n, size_t(1) << 16);
+    std::vector<uint32_t> h(blk * 8);
+    uint64_t state = 0x5eed0fba5e11ull;
+    auto next = [&state]() {
+        uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    for (size_t e = 0; e < blk; e++) {
+        uint32_t x[8];
+        for (;;) {
+            for (int w = 0; w < 4; w++) {
+                const uint64_t v = next();
+                x[2 * w] = uint32_t(v);
+                x[2 * w + 1] = uint32_t(v >> 32);
+            }
+            for (int b = top + 1; b < 256; b++) x[b / 32] &= ~(1u << (b % 32));
+            int i = 7;
+            while (i > 0 && x[i] == r[i]) i--;
+            if (x[i] < r[i]) break;  // below r: accept
+        }
+        for (int k = 0; k < 8; k++) h[e * 8 + k] = x[k];
+    }
+    if (cudaMemcpy(d, h.data(), blk * 32, cudaMemcpyHostToDevice) != cudaSuccess) return ZKNTT_ECUDA;
+    for (size_t done = blk; done < n; done *= 2) {
+        const size_t c = std::min(done, n - done);
+        if (cudaMemcpy(static_cast<char *>(d) + done * 32, d, c * 32, cudaMemcpyDeviceToDevice) !=
+            cudaSuccess)
+            return ZKNTT_ECUDA;
+    }
+    return ZKNTT_OK;
+}
+
+zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_candidates,
                                    zkntt_tune_result *best) {
     if (field < 0 || field >= NUM_FIELDS) return ZKNTT_EINVAL;
     if (log_n < 1 || log_n > 28 || max_candidates < 1) return ZKNTT_EINVAL;
@@ -208,7 +254,7 @@ extern "C" zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, 
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         result = ZKNTT_ENOMEM;
     }
-    if (result == ZKNTT_OK) cudaMemset(in, 0, bytes);
+    if (result == ZKNTT_OK) result = fill_uniform(field, in, size_t(1) << log_n);
     TuneEntry bestE;
     double best_ms = 1e30;
     for (size_t ci = 0; ci < cands.size() && result == ZKNTT_OK; ci++) {

@@ -223,12 +223,22 @@ uint32_t rev_bits(uint32_t x, int bits) {
 }
 
 // ---------------------------------------------------------------------------
+// Device-side error words: one per stream that ran a persistent batch launch,
+// taken from a fixed slab allocated at device set-up (so a launch never
+// allocates one, and a capture never sees an allocation for it).  Streams
+// beyond the slab share its last word.
+constexpr int STATUS_WORDS = 1024;
+
 struct DeviceInfo {
     int sms = 0;
     // batch kernel occupancy per field for 2^(10+i) bytes of shared memory
     int batch_blocks_per_sm[NUM_FIELDS][8] = {};
     bool init = false;
-    uint32_t *status = nullptr;  // sticky device-side error word
+    uint32_t *status_slab = nullptr;             // STATUS_WORDS sticky error words
+    std::map<uintptr_t, int> status_of_stream;   // stream handle -> word index
+    // the library's own stream-ordered pool for scratch (the device's default
+    // pool, which other code in the process shares, is left as it is)
+    cudaMemPool_t pool = nullptr;
 };
 
 std::mutex g_dev_mu;
@@ -255,23 +265,55 @@ zkntt_status device_info(DeviceInfo **out) {
                 d.batch_blocks_per_sm[f][i] = std::max(d.batch_blocks_per_sm[f][i], 1);
             }
         }
-        ZK_CHECK(cudaMalloc(&d.status, sizeof(uint32_t)));
-        ZK_CHECK(cudaMemset(d.status, 0, sizeof(uint32_t)));
-        // keep freed stream-ordered scratch in the pool between executions, and
-        // never hand a block freed on one stream to another stream behind an
-        // inserted wait: calls on different streams (the host-buffer path,
-        // concurrent batches) must stay independent; the pool grows instead
-        cudaMemPool_t pool;
-        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-            uint64_t thr = UINT64_MAX;
-            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-            int no = 0;
-            cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
-        }
+        ZK_CHECK(cudaMalloc(&d.status_slab, STATUS_WORDS * sizeof(uint32_t)));
+        ZK_CHECK(cudaMemset(d.status_slab, 0, STATUS_WORDS * sizeof(uint32_t)));
+        // A private pool: freed scratch stays in it between executions (no
+        // release threshold), and a block freed on one stream is never handed
+        // to another stream behind an inserted wait -- calls on different
+        // streams (the host-buffer path, concurrent batches) stay independent;
+        // the pool grows instead.
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        ZK_CHECK(cudaMemPoolCreate(&d.pool, &props));
+        uint64_t thr = UINT64_MAX;
+        ZK_CHECK(cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        int no = 0;
+        ZK_CHECK(cudaMemPoolSetAttribute(d.pool, cudaMemPoolReuseAllowInternalDependencies, &no));
         d.init = true;
     }
     *out = &d;
     return ZKNTT_OK;
+}
+
+// the error word of stream s on the current device (assigned on first use)
+uint32_t *status_word(DeviceInfo *d, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    const uintptr_t key = reinterpret_cast<uintptr_t>(s);
+    auto it = d->status_of_stream.find(key);
+    int idx;
+    if (it != d->status_of_stream.end()) {
+        idx = it->second;
+    } else {
+        idx = std::min<int>(int(d->status_of_stream.size()), STATUS_WORDS - 1);
+        d->status_of_stream[key] = idx;
+    }
+    return d->status_slab + idx;
+}
+
+// Stream-ordered scratch from the library's pool.  Inside a stream capture the
+// allocation becomes a graph allocation node (cudaMallocAsync), which draws on
+// graph-owned memory rather than on any pool's.
+zkntt_status pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+    DeviceInfo *dev;
+    zkntt_status st = device_info(&dev);
+    if (st != ZKNTT_OK) return st;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    ZK_CHECK(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return from_cuda(cudaMallocAsync(p, bytes, s));
+    return from_cuda(cudaMallocFromPoolAsync(p, bytes, dev->pool, s));
 }
 
 }  // namespace
@@ -610,6 +652,16 @@ bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb) {
     return x < y + nb && y < x + na;
 }
 
+// A plan's tables live on the device it was created on: executing it while
+// another device is current would pair them with that device's stream and
+// scratch.  EINVAL (nothing enqueued) when the current device differs;
+// ECUDA when the current device cannot be read.
+zkntt_status check_plan_device(const zkntt_plan_s *P) {
+    int cur = 0;
+    ZK_CHECK(cudaGetDevice(&cur));
+    return cur == P->device ? ZKNTT_OK : ZKNTT_EINVAL;
+}
+
 zkntt_status run_passes(const zkntt_plan_s *P, const void *in, void *out, void *scratch,
                         cudaStream_t s) {
     const FieldKernels &kk = field_kernels(P->field);
@@ -634,9 +686,8 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 
-zkntt_status noalloc_scratch(void **out) {
-    int dev = 0;
-    ZK_CHECK(cudaGetDevice(&dev));
+// (called with the plan's device current: check_plan_device has passed)
+zkntt_status noalloc_scratch(int dev, void **out) {
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return ZKNTT_EUNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
@@ -798,12 +849,12 @@ zkntt_status launch_batch_field(const std::vector<JobSpec> &jobs, cudaStream_t s
 
     uint32_t *ctrl = nullptr;
     const size_t words = 2 + segs.size();
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&ctrl), words * 4, s);
-    if (e != cudaSuccess) {
+    st = pool_alloc(reinterpret_cast<void **>(&ctrl), words * 4, s);
+    if (st != ZKNTT_OK) {
         delete tab;
-        return from_cuda(e);
+        return st;
     }
-    e = cudaMemsetAsync(ctrl, 0, words * 4, s);
+    cudaError_t e = cudaMemsetAsync(ctrl, 0, words * 4, s);
     if (e == cudaSuccess) {
         // shared memory for the largest tile of the launch; occupancy comes from
         // the table built at device set-up (no query here: this path must stay
@@ -830,7 +881,7 @@ zkntt_status launch_batch_field(const std::vector<JobSpec> &jobs, cudaStream_t s
                                                      std::min<uint32_t>(item, dev->sms)));
         }
         uint32_t *done = ctrl + 2;
-        uint32_t *status = dev->status;
+        uint32_t *status = status_word(dev, s);
         void *args[] = {tab, &ctrl, &done, &status};
         if (e == cudaSuccess && grid > 0)
             e = cudaLaunchKernel(batch_kernel_ptr(field), dim3(grid), dim3(BATCH_THREADS), args,
@@ -977,6 +1028,7 @@ zkntt_status zkntt_plan_describe(zkntt_plan plan, int *num_passes, int digit_bit
 zkntt_status zkntt_execute_scratch(zkntt_plan plan, const void *d_in, void *d_out, void *d_scratch,
                                    size_t scratch_bytes, void *stream) {
     if (!plan || bad_ptr(d_in) || bad_ptr(d_out)) return ZKNTT_EINVAL;
+    if (zkntt_status dc = check_plan_device(plan)) return dc;
     const size_t bytes = size_t(32) << plan->log_n;
     if (partial_overlap(d_in, d_out, bytes)) return ZKNTT_EINVAL;
     const size_t need = scratch_bytes_of(plan);
@@ -990,12 +1042,16 @@ zkntt_status zkntt_execute_scratch(zkntt_plan plan, const void *d_in, void *d_ou
 
 zkntt_status zkntt_execute(zkntt_plan plan, const void *d_in, void *d_out, void *stream) {
     if (!plan || bad_ptr(d_in) || bad_ptr(d_out)) return ZKNTT_EINVAL;
+    if (zkntt_status dc = check_plan_device(plan)) return dc;
     const size_t bytes = size_t(32) << plan->log_n;
     if (partial_overlap(d_in, d_out, bytes)) return ZKNTT_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t need = scratch_bytes_of(plan);
     void *scratch = nullptr;
-    if (need) ZK_CHECK(cudaMallocAsync(&scratch, need, s));
+    if (need) {
+        zkntt_status sa = pool_alloc(&scratch, need, s);
+        if (sa != ZKNTT_OK) return sa;
+    }
     zkntt_status st = run_passes(plan, d_in, d_out, scratch, s);
     if (scratch) {
         zkntt_status st2 = from_cuda(cudaFreeAsync(scratch, s));
@@ -1006,11 +1062,13 @@ zkntt_status zkntt_execute(zkntt_plan plan, const void *d_in, void *d_out, void 
 
 zkntt_status zkntt_execute_host(zkntt_plan plan, const void *h_in, void *h_out, void *stream) {
     if (!plan || !h_in || !h_out) return ZKNTT_EINVAL;
+    if (zkntt_status dc = check_plan_device(plan)) return dc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t bytes = size_t(32) << plan->log_n;
     const size_t need = scratch_bytes_of(plan);
     char *buf = nullptr;
-    ZK_CHECK(cudaMallocAsync(reinterpret_cast<void **>(&buf), bytes + need, s));
+    zkntt_status sa = pool_alloc(reinterpret_cast<void **>(&buf), bytes + need, s);
+    if (sa != ZKNTT_OK) return sa;
     zkntt_status st = from_cuda(cudaMemcpyAsync(buf, h_in, bytes, cudaMemcpyHostToDevice, s));
     if (st == ZKNTT_OK) st = run_passes(plan, buf, buf, need ? buf + bytes : nullptr, s);
     if (st == ZKNTT_OK) st = from_cuda(cudaMemcpyAsync(h_out, buf, bytes, cudaMemcpyDeviceToHost, s));
@@ -1021,6 +1079,7 @@ zkntt_status zkntt_execute_host(zkntt_plan plan, const void *h_in, void *h_out, 
 zkntt_status zkntt_execute_host_buffered(zkntt_plan plan, const void *h_in, void *h_out,
                                          void *d_work, size_t work_bytes, void *stream) {
     if (!plan || !h_in || !h_out || bad_ptr(d_work)) return ZKNTT_EINVAL;
+    if (zkntt_status dc = check_plan_device(plan)) return dc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t bytes = size_t(32) << plan->log_n;
     const size_t need = scratch_bytes_of(plan);
@@ -1034,13 +1093,14 @@ zkntt_status zkntt_execute_host_buffered(zkntt_plan plan, const void *h_in, void
 
 zkntt_status zkntt_execute_noalloc(zkntt_plan plan, const void *d_in, void *d_out, void *stream) {
     if (!plan || bad_ptr(d_in) || bad_ptr(d_out)) return ZKNTT_EINVAL;
+    if (zkntt_status dc = check_plan_device(plan)) return dc;
     const size_t bytes = size_t(32) << plan->log_n;
     if (partial_overlap(d_in, d_out, bytes)) return ZKNTT_EINVAL;
     const size_t need = scratch_bytes_of(plan);
     if (need > ZKNTT_NOALLOC_SCRATCH_BYTES) return ZKNTT_EINVAL;
     void *scratch = nullptr;
     if (need) {
-        zkntt_status st = noalloc_scratch(&scratch);
+        zkntt_status st = noalloc_scratch(plan->device, &scratch);
         if (st != ZKNTT_OK) return st;
     }
     return run_passes(plan, d_in, d_out, scratch, static_cast<cudaStream_t>(stream));
@@ -1054,12 +1114,16 @@ zkntt_status zkntt_execute_batch(const zkntt_plan *plans, const zkntt_io *ptrs, 
     size_t scratch_total = 0;
     for (int j = 0; j < count; j++) {
         if (!plans[j] || bad_ptr(ptrs[j].d_in) || bad_ptr(ptrs[j].d_out)) return ZKNTT_EINVAL;
+        if (zkntt_status dc = check_plan_device(plans[j])) return dc;
         const size_t bytes = size_t(32) << plans[j]->log_n;
         if (partial_overlap(ptrs[j].d_in, ptrs[j].d_out, bytes)) return ZKNTT_EINVAL;
         scratch_total += scratch_bytes_of(plans[j]);
     }
     char *scratch = nullptr;
-    if (scratch_total) ZK_CHECK(cudaMallocAsync(reinterpret_cast<void **>(&scratch), scratch_total, s));
+    if (scratch_total) {
+        zkntt_status sa = pool_alloc(reinterpret_cast<void **>(&scratch), scratch_total, s);
+        if (sa != ZKNTT_OK) return sa;
+    }
     std::vector<JobSpec> jobs(count);
     size_t off = 0;
     for (int j = 0; j < count; j++) {
@@ -1097,6 +1161,7 @@ zkntt_status zkntt_execute_batch_signal(const zkntt_plan *plans, const zkntt_io 
     size_t scratch_total = 0;
     for (int j = 0; j < count; j++) {
         if (!plans[j] || bad_ptr(ptrs[j].d_in) || bad_ptr(ptrs[j].d_out)) return ZKNTT_EINVAL;
+        if (zkntt_status dc = check_plan_device(plans[j])) return dc;
         const size_t bytes = size_t(32) << plans[j]->log_n;
         if (partial_overlap(ptrs[j].d_in, ptrs[j].d_out, bytes)) return ZKNTT_EINVAL;
         scratch_total += scratch_bytes_of(plans[j]);
@@ -1107,7 +1172,10 @@ zkntt_status zkntt_execute_batch_signal(const zkntt_plan *plans, const zkntt_io 
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return plans[a]->log_n < plans[b]->log_n; });
     char *scratch = nullptr;
-    if (scratch_total) ZK_CHECK(cudaMallocAsync(reinterpret_cast<void **>(&scratch), scratch_total, s));
+    if (scratch_total) {
+        zkntt_status sa = pool_alloc(reinterpret_cast<void **>(&scratch), scratch_total, s);
+        if (sa != ZKNTT_OK) return sa;
+    }
     zkntt_status st = ZKNTT_OK;
     size_t off = 0, b = 0;
     while (b < order.size() && st == ZKNTT_OK) {
@@ -1184,7 +1252,8 @@ zkntt_status zkntt_groth16_h(zkntt_field field, int log_n, const void *d_a, cons
         for (int k = 0; k < 3; k++)
             if ((st = zkntt_execute(G->cntt, sv[k], sv[k], s))) return st;
         uint4 *z = nullptr;
-        ZK_CHECK(cudaMallocAsync(reinterpret_cast<void **>(&z), 32, s));
+        zkntt_status sa = pool_alloc(reinterpret_cast<void **>(&z), 32, s);
+        if (sa != ZKNTT_OK) return sa;
         st = from_cuda(cudaMemcpyAsync(z, G->zinv.data(), 32, cudaMemcpyHostToDevice, s));
         if (st == ZKNTT_OK) st = launch_pointwise(field, S0, S1, S2, z, d_h, size_t(1) << log_n, s);
         zkntt_status st2 = from_cuda(cudaFreeAsync(z, s));
@@ -1198,7 +1267,10 @@ zkntt_status zkntt_groth16_h(zkntt_field field, int log_n, const void *d_a, cons
     //   job 6:    cosetINTT_g(S0*S1 - S2) * zinv -> h   levels 2p .. 3p-1
     const size_t per = scratch_bytes_of(G->ntt);
     char *ps = nullptr;
-    if (per) ZK_CHECK(cudaMallocAsync(reinterpret_cast<void **>(&ps), 7 * per, s));
+    if (per) {
+        zkntt_status sa = pool_alloc(reinterpret_cast<void **>(&ps), 7 * per, s);
+        if (sa != ZKNTT_OK) return sa;
+    }
     std::vector<JobSpec> jobs(7);
     const int p1 = G->intt_gj->passes, p2 = G->ntt->passes;
     for (int k = 0; k < 3; k++) {
@@ -1302,21 +1374,23 @@ zkntt_status zkntt_last_cuda_error(int *err) {
 }
 
 zkntt_status zkntt_sync_status(void *stream) {
-    ZK_CHECK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ZK_CHECK(cudaStreamSynchronize(s));
     DeviceInfo *dev;
     zkntt_status st = device_info(&dev);
     if (st != ZKNTT_OK) return st;
+    uint32_t *w = status_word(dev, s);
     uint32_t word = 0;
-    ZK_CHECK(cudaMemcpy(&word, dev->status, 4, cudaMemcpyDeviceToHost));
+    ZK_CHECK(cudaMemcpy(&word, w, 4, cudaMemcpyDeviceToHost));
     if (word) {
-        ZK_CHECK(cudaMemset(dev->status, 0, 4));
+        ZK_CHECK(cudaMemset(w, 0, 4));
         if (word & BATCH_STATUS_TIMEOUT) return ZKNTT_ETIMEOUT;
         return ZKNTT_ECUDA;
     }
     return ZKNTT_OK;
 }
 
-zkntt_status zkntt_selftest_timeout(int timeout_ms, void *stream) {
+zkntt_status zkntt_inject_timeout(int timeout_ms, void *stream) {
     if (timeout_ms < 1 || timeout_ms > 10000) return ZKNTT_EINVAL;
     DeviceInfo *dev;
     zkntt_status st = device_info(&dev);
@@ -1336,18 +1410,106 @@ zkntt_status zkntt_selftest_timeout(int timeout_ms, void *stream) {
     tab->seg[0].dep[1] = tab->seg[0].dep[2] = -1;
     tab->seg[0].dep_tiles[0] = 1;
     uint32_t *ctrl = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&ctrl), 3 * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctrl, 0, 3 * 4, s);
+    st = pool_alloc(reinterpret_cast<void **>(&ctrl), 3 * 4, s);
+    if (st != ZKNTT_OK) {
+        delete tab;
+        return st;
+    }
+    cudaError_t e = cudaMemsetAsync(ctrl, 0, 3 * 4, s);
     if (e == cudaSuccess) {
         uint32_t *done = ctrl + 2;
-        uint32_t *status = dev->status;
+        uint32_t *status = status_word(dev, s);
         void *args[] = {tab, &ctrl, &done, &status};
         e = cudaLaunchKernel(batch_kernel_ptr(0), dim3(1), dim3(BATCH_THREADS), args, 64 * 1024, s);
     }
     if (ctrl) cudaFreeAsync(ctrl, s);
     delete tab;
-    if (e != cudaSuccess) return from_cuda(e);
+    return from_cuda(e);
+}
+
+zkntt_status zkntt_selftest_timeout(int timeout_ms, void *stream) {
+    zkntt_status st = zkntt_inject_timeout(timeout_ms, stream);
+    if (st != ZKNTT_OK) return st;
     return zkntt_sync_status(stream);
+}
+
+zkntt_status zkntt_selftest_device_check(int *checked, int *rejected) {
+    if (!checked || !rejected) return ZKNTT_EINVAL;
+    *checked = *rejected = 0;
+    int cur = 0;
+    ZK_CHECK(cudaGetDevice(&cur));
+    // a real plan and real buffers of 16 elements: were a check missing, the
+    // call would run a valid transform on them
+    zkntt_plan real = nullptr;
+    zkntt_status st = create_plan(&real, ZKNTT_BLS12_381_FR, 4, ZKNTT_FORWARD, nullptr, nullptr, nullptr);
+    if (st != ZKNTT_OK) return st;
+    char *buf = nullptr;
+    st = from_cuda(cudaMalloc(&buf, 4 * 512));
+    if (st != ZKNTT_OK) {
+        free_plan(real);
+        return st;
+    }
+    char *hbuf = nullptr;
+    st = from_cuda(cudaMallocHost(&hbuf, 2 * 512));
+    if (st != ZKNTT_OK) {
+        cudaFree(buf);
+        free_plan(real);
+        return st;
+    }
+    zkntt_plan_s *fake = new (std::nothrow) zkntt_plan_s;
+    if (!fake) {
+        cudaFreeHost(hbuf);
+        cudaFree(buf);
+        free_plan(real);
+        return ZKNTT_ENOMEM;
+    }
+    *fake = *real;
+    fake->allocs.clear();       // the tables belong to `real`
+    fake->device = cur + 1;     // as if created on another device
+    zkntt_plan plans[1] = {fake};
+    zkntt_io io[1] = {{buf, buf + 512}};
+    uint32_t *flags = reinterpret_cast<uint32_t *>(buf + 3 * 512);
+    const zkntt_status got[] = {
+        zkntt_execute(fake, buf, buf + 512, nullptr),
+        zkntt_execute_scratch(fake, buf, buf + 512, buf + 1024, 512, nullptr),
+        zkntt_execute_host(fake, hbuf, hbuf + 512, nullptr),
+        zkntt_execute_host_buffered(fake, hbuf, hbuf + 512, buf, 2048, nullptr),
+        zkntt_execute_noalloc(fake, buf, buf + 512, nullptr),
+        zkntt_execute_batch(plans, io, 1, nullptr),
+        zkntt_execute_batch_signal(plans, io, 1, flags, 1, nullptr),
+    };
+    for (zkntt_status g : got) {
+        (*checked)++;
+        if (g == ZKNTT_EINVAL) (*rejected)++;
+    }
+    delete fake;
+    st = from_cuda(cudaDeviceSynchronize());
+    cudaFreeHost(hbuf);
+    cudaFree(buf);
+    free_plan(real);
+    return st;
+}
+
+zkntt_status zkntt_pool_info(size_t *reserved_bytes, size_t *used_bytes) {
+    if (!reserved_bytes || !used_bytes) return ZKNTT_EINVAL;
+    DeviceInfo *dev;
+    zkntt_status st = device_info(&dev);
+    if (st != ZKNTT_OK) return st;
+    uint64_t r = 0, u = 0;
+    ZK_CHECK(cudaMemPoolGetAttribute(dev->pool, cudaMemPoolAttrReservedMemCurrent, &r));
+    ZK_CHECK(cudaMemPoolGetAttribute(dev->pool, cudaMemPoolAttrUsedMemCurrent, &u));
+    *reserved_bytes = size_t(r);
+    *used_bytes = size_t(u);
+    return ZKNTT_OK;
+}
+
+zkntt_status zkntt_imadbench(int mode, int blocks, int threads, int iters, void *d_sink,
+                             void *stream) {
+    if (mode < 0 || mode > 1) return ZKNTT_EINVAL;
+    if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !d_sink) return ZKNTT_EINVAL;
+    void *args[] = {&mode, &iters, &d_sink};
+    return from_cuda(cudaLaunchKernel(imadbench_kernel_ptr(), dim3(blocks), dim3(threads), args, 0,
+                                      static_cast<cudaStream_t>(stream)));
 }
 
 zkntt_status zkntt_field_info(zkntt_field field, uint32_t modulus[8], uint32_t generator_mont[8],
@@ -1383,7 +1545,8 @@ zkntt_status zkntt_pointwise(zkntt_field field, const void *d_a, const void *d_b
     if (bad_ptr(d_a) || bad_ptr(d_b) || bad_ptr(d_c) || bad_ptr(d_h)) return ZKNTT_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     void *z = nullptr;
-    ZK_CHECK(cudaMallocAsync(&z, 32, s));
+    zkntt_status sa = pool_alloc(&z, 32, s);
+    if (sa != ZKNTT_OK) return sa;
     zkntt_status st = from_cuda(cudaMemcpyAsync(z, z_mont, 32, cudaMemcpyHostToDevice, s));
     if (st == ZKNTT_OK) st = launch_pointwise(field, d_a, d_b, d_c, z, d_h, n, s);
     zkntt_status st2 = from_cuda(cudaFreeAsync(z, s));

@@ -8,7 +8,9 @@ device memory, admits requests while others run, and packs everything admitted
 into the next persistent batch launch:
 
 * admission: a request enters when its device footprint (output vector plus
-  scratch) fits in the memory budget; otherwise it waits, in arrival order;
+  its plan's scratch) fits in the memory budget and, with a GPU executor, in
+  the device memory free at that moment (read live, less a reserve);
+  otherwise it waits, in arrival order;
 * batching: whenever one of the compute streams is idle, all admitted,
   unstarted requests (up to ``max_batch_jobs``) go out as ONE
   ``zkntt_execute_batch`` launch on that stream; with two streams, a batch
@@ -66,10 +68,11 @@ class Request:
 
 
 def footprint_bytes(log_n: int) -> int:
-    """Device bytes a request holds while admitted: its output vector plus the
-    multi-pass scratch the batch launch takes from the pool."""
+    """Device bytes a request may hold while admitted, when the executor cannot
+    say exactly: its output vector plus one vector of scratch (the most a plan
+    of any schedule takes from the pool)."""
     n = 1 << log_n
-    return 32 * n + (32 * n if log_n > 11 else 0)
+    return 32 * n + 32 * n
 
 
 @dataclass
@@ -115,6 +118,10 @@ class Engine:
         self.solo_log_n = solo_log_n
         self.can_solo = hasattr(executor, "launch_solo")
 
+    def _footprint(self, r: Request) -> int:
+        fp = getattr(self.ex, "footprint", None)
+        return fp(r) if fp is not None else footprint_bytes(r.log_n)
+
     def _is_big(self, r: Request) -> bool:
         return self.can_solo and self.solo_log_n is not None and r.log_n >= self.solo_log_n
 
@@ -135,8 +142,10 @@ class Engine:
         closed test)."""
         arrivals = sorted(requests, key=lambda r: (r.arrival_s, r.rid))
         for r in arrivals:
-            if footprint_bytes(r.log_n) > self.budget:
+            r._fp = self._footprint(r)
+            if r._fp > self.budget:
                 raise ValueError(f"request {r.rid} (2^{r.log_n}) can never fit the memory budget")
+        headroom = getattr(self.ex, "headroom_bytes", None)
         waiting: deque[Request] = deque()      # arrived, not admitted
         ready: deque[Request] = deque()        # admitted, not launched
         inflight: list = []     # (token, stream, requests, not yet retired) per busy stream
@@ -165,7 +174,7 @@ class Engine:
                         if fin is None:
                             fin = self.clock() - t0
                         r.finish_s = fin
-                        used -= footprint_bytes(r.log_n)
+                        used -= r._fp
                         self.ex.release(r)
                         done.append(r)
                         live.remove(r)
@@ -174,13 +183,21 @@ class Engine:
                 else:
                     still.append((token, stream, reqs, live))
             inflight = still
-            # admission in arrival order while memory allows
-            while waiting and used + footprint_bytes(waiting[0].log_n) <= self.budget:
-                r = waiting.popleft()
-                r.admit_s = self.clock() - t0
-                used += footprint_bytes(r.log_n)
-                peak = max(peak, used)
-                ready.append(r)
+            # admission in arrival order while memory allows: within the
+            # budget, and (with a live executor) within the device memory
+            # free right now, less what admitted but unlaunched requests will
+            # still take
+            if waiting and used + waiting[0]._fp <= self.budget:
+                live = headroom() - sum(q._fp for q in ready) if headroom is not None else None
+                while waiting and used + waiting[0]._fp <= self.budget and \
+                        (live is None or waiting[0]._fp <= live):
+                    r = waiting.popleft()
+                    r.admit_s = self.clock() - t0
+                    used += r._fp
+                    if live is not None:
+                        live -= r._fp
+                    peak = max(peak, used)
+                    ready.append(r)
             # launch: everything ready goes out on an idle stream
             while ready and free_streams:
                 stream = free_streams.pop(0)
@@ -240,7 +257,7 @@ class GpuExecutor:
     memory for batches, a CUDA event per launch."""
 
     def __init__(self, device=0, streams: int = 2, input_pool=None, keep_outputs: bool = True,
-                 flag_slots: int = 4096):
+                 flag_slots: int = 4096, reserve_bytes: int = 2 << 30):
         import torch
 
         import paper_2509_22684_gb300 as zk
@@ -254,6 +271,23 @@ class GpuExecutor:
         self.flags = zk.CompletionFlags(flag_slots)
         self.next_slot = 0
         self.epoch = 0
+        self.reserve = reserve_bytes
+
+    def footprint(self, r: Request) -> int:
+        """Device bytes the request takes while admitted: its output vector and
+        the scratch its own plan needs (zkntt_plan_scratch_bytes)."""
+        p = self.plan(r.field, r.log_n, r.kind)
+        return 32 * p.n + p.scratch_bytes()
+
+    def headroom_bytes(self) -> int:
+        """Device memory the engine may still admit against, read live: free
+        device memory, plus what torch's caching allocator and the library's
+        scratch pool hold but have not handed out, less a reserve."""
+        torch = self.torch
+        free, _ = torch.cuda.mem_get_info(self.device)
+        cached = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
+        pool_reserved, pool_used = self.zk.pool_info()
+        return free + cached + (pool_reserved - pool_used) - self.reserve
 
     def plan(self, field_name: str, log_n: int, kind: str):
         key = (field_name, log_n, kind)

@@ -71,6 +71,11 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.zkntt_last_cuda_error(ctypes.byref(err)) == N.OK
     assert lib.zkntt_field_op(0, 5, None, None, None, 1, None) == N.EINVAL
     assert lib.zkntt_selftest_timeout(0, None) == N.EINVAL
+    assert lib.zkntt_inject_timeout(0, None) == N.EINVAL
+    assert lib.zkntt_inject_timeout(10001, None) == N.EINVAL
+    assert lib.zkntt_imadbench(2, 1, 32, 1, ctypes.c_void_p(256), None) == N.EINVAL
+    assert lib.zkntt_imadbench(0, 1, 32, 1, None, None) == N.EINVAL
+    assert lib.zkntt_selftest_device_check(None, None) == N.EINVAL
 
 
 def test_field_info_without_gpu(lib):

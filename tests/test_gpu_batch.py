@@ -1,6 +1,8 @@
 """Persistent batch launch and the Groth16 H sequence: every result equals the
 oracle's and the solo execution's, bit for bit; the bounded device wait
 reports a timeout instead of hanging."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -121,6 +123,31 @@ def test_bounded_wait_reports_timeout():
     with zk.Plan(F.name, 12) as p:
         assert np.array_equal(to_host(p.execute(x)), ref.ntt_mont(F, X))
     zk.sync_status()
+
+
+def test_timeout_is_reported_on_its_own_stream_only():
+    """Each stream has its own device-side error word: a bounded wait that
+    gives up on stream A is reported by zkntt_sync_status(A), not by a
+    concurrent stream B, and reading it clears it."""
+    import torch
+    from paper_2509_22684_gb300 import _native as N
+    a, b = torch.cuda.Stream(), torch.cuda.Stream()
+    ha, hb = ctypes.c_void_p(a.cuda_stream), ctypes.c_void_p(b.cuda_stream)
+    assert N.lib().zkntt_inject_timeout(20, ha) == N.OK
+    assert N.lib().zkntt_sync_status(hb) == N.OK
+    assert N.lib().zkntt_sync_status(ha) == N.ETIMEOUT
+    assert N.lib().zkntt_sync_status(ha) == N.OK
+
+
+def test_plan_of_another_device_is_rejected_before_enqueue():
+    """Every execute entry point returns EINVAL for a plan whose device is not
+    the current one (the self-test passes each of them a copy of a real plan
+    marked as another device's)."""
+    from paper_2509_22684_gb300 import _native as N
+    checked, rejected = ctypes.c_int(), ctypes.c_int()
+    assert N.lib().zkntt_selftest_device_check(ctypes.byref(checked), ctypes.byref(rejected)) == N.OK
+    assert checked.value == 7
+    assert rejected.value == 7
 
 
 @pytest.mark.parametrize("L", [10, 16])

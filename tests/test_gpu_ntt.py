@@ -88,15 +88,60 @@ def test_configured_sizes_full_vector(F, L, kind):
     assert np.array_equal(got, want), first_mismatch(got, want)
 
 
-@pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
-@pytest.mark.parametrize("mode", ["precomp", "otf"])
-def test_2_24_full_vector(F, mode):
+_BIG_INPUT = {}
+
+
+def _big_input(F, L, seed):
+    """Seeded input of 2^L elements, kept for the next test of the same field
+    and size (one entry: a 2^26 vector is 2 GiB of host memory)."""
+    key = (F.name, L, seed)
+    if key not in _BIG_INPUT:
+        _BIG_INPUT.clear()
+        _BIG_INPUT[key] = rand_dev(F, L, seed)[0]
+    return _BIG_INPUT[key]
+
+
+# the tests of one field and size run one after the other, so the input is
+# drawn once per (field, size)
+_CASES_24 = [(F, kind, mode) for F in FIELDS for kind in KINDS for mode in ("precomp", "otf")]
+
+
+@pytest.mark.parametrize("F,kind,mode", _CASES_24,
+                         ids=[f"{F.name}-{k}-{m}" for F, k, m in _CASES_24])
+def test_2_24_full_vector(F, kind, mode):
+    """2^24, every kind in both twiddle modes: the whole output equals the C
+    oracle's (Section II-B transform; coset kinds as in Fig. 2)."""
     L = 24
-    X, x = rand_dev(F, L, 2024)
-    with _plan(F, L, "ntt", twiddle_mode=mode) as p:
-        y = p.execute(x)
+    X = _big_input(F, L, 2024)
+    with _plan(F, L, kind, twiddle_mode=mode) as p:
+        y = p.execute(to_dev(X))
     got = to_host(y)
-    want = cpu.ntt(F, X)
+    del y
+    want = _oracle(F, X, kind)
+    assert np.array_equal(got, want), first_mismatch(got, want)
+
+
+_CASES_26 = [(F, kind, "precomp") for F in FIELDS for kind in KINDS] + \
+    [(fld.BLS12_381, "coset_intt", "otf"), (fld.BN254, "ntt", "otf")]
+
+
+@pytest.mark.parametrize("F,kind,mode", _CASES_26,
+                         ids=[f"{F.name}-{k}-{m}" for F, k, m in _CASES_26])
+def test_2_26_full_vector(F, kind, mode):
+    """2^26 (the largest size of the plain-transform grid), every kind: the
+    whole output equals the C oracle's.  A round trip alone would miss a
+    mistake shared by a forward and an inverse plan (a wrong root, table
+    index or digit split at this size); this comparison does not."""
+    import torch
+    L = 26
+    X = _big_input(F, L, 2026)
+    with _plan(F, L, kind, twiddle_mode=mode) as p:
+        assert p.describe()["twiddle_mode"] == mode
+        y = p.execute(to_dev(X))
+        got = to_host(y)
+        del y
+        torch.cuda.empty_cache()
+    want = _oracle(F, X, kind)
     assert np.array_equal(got, want), first_mismatch(got, want)
 
 

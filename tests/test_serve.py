@@ -158,3 +158,45 @@ def test_without_launch_solo_everything_is_batched():
     ex = FakeExecutor(per_elem_s=1e-9, overhead_s=1e-4)
     done, st = Engine(ex, budget_bytes=1 << 32, streams=2, solo_log_n=12).run(reqs)
     assert st.requests == len(reqs)
+
+
+class LiveMemoryExecutor(FakeExecutor):
+    """A device with a fixed amount of memory: launched requests hold their
+    footprint until released; the engine sees only the live headroom."""
+
+    def __init__(self, capacity, **kw):
+        super().__init__(**kw)
+        self.capacity = capacity
+        self.held = 0
+        self.max_held = 0
+
+    def footprint(self, r):
+        # single-pass sizes need no scratch, like a plan of one pass
+        return 32 * r.n + (32 * r.n if r.log_n > 13 else 0)
+
+    def headroom_bytes(self):
+        return self.capacity - self.held
+
+    def launch(self, reqs, stream):
+        for r in reqs:
+            self.held += self.footprint(r)
+        self.max_held = max(self.max_held, self.held)
+        return super().launch(reqs, stream)
+
+    def release(self, r):
+        self.held -= self.footprint(r)
+        super().release(r)
+
+
+def test_admission_follows_live_device_memory_and_the_plans_footprint():
+    """With an executor that reports live headroom, admitted work never holds
+    more device memory than there is, even under a far larger budget, and the
+    footprint comes from the executor (the plan's own scratch), not from a
+    size threshold."""
+    reqs = _trace(count=200, rate=20000.0, lmin=12, lmax=16)
+    ex = LiveMemoryExecutor(capacity=3 * 64 * (1 << 16))
+    done, st = Engine(ex, budget_bytes=1 << 40, streams=2).run(reqs)
+    assert st.requests == len(reqs)
+    assert ex.max_held <= ex.capacity
+    assert ex.held == 0
+    assert st.peak_bytes <= ex.capacity

@@ -26,19 +26,23 @@ def _noalloc(plan, x, y):
     return st
 
 
-@pytest.mark.parametrize("F,L,kind", [
-    (fld.BLS12_381, 10, "ntt"),        # single pass: no scratch involved
-    (fld.BLS12_381, 16, "ntt"),        # two passes
-    (fld.BN254, 18, "coset_intt"),
-    (fld.BLS12_381, 20, "intt"),       # largest size the static scratch holds
+@pytest.mark.parametrize("F,L,kind,digits,single", [
+    (fld.BLS12_381, 8, "ntt", None, True),     # below the tuned sizes: one pass, no scratch
+    (fld.BLS12_381, 10, "ntt", (10,), True),   # forced single pass: no scratch
+    (fld.BLS12_381, 10, "ntt", None, False),   # the tuned schedule has two passes
+    (fld.BLS12_381, 16, "ntt", None, False),
+    (fld.BN254, 18, "coset_intt", None, False),
+    (fld.BLS12_381, 20, "intt", None, False),  # largest size the static scratch holds
 ])
-def test_noalloc_matches_execute_on_two_consecutive_calls(F, L, kind):
+def test_noalloc_matches_execute_on_two_consecutive_calls(F, L, kind, digits, single):
     import torch
     import paper_2509_22684_gb300 as zk
     from paper_2509_22684_gb300 import _native as N
     inverse = kind.endswith("intt")
     shift = F.to_mont(F.g) if kind.startswith("coset") else None
-    with zk.Plan(F.name, L, inverse=inverse, coset_shift=shift) as p:
+    with zk.Plan(F.name, L, inverse=inverse, coset_shift=shift, digits=digits) as p:
+        assert (p.describe()["passes"] == 1) == single
+        assert (p.scratch_bytes() == 0) == single
         for call, seed in enumerate((501, 502)):
             X = uniform_elements(F.r, 1 << L, seed + L)
             x = to_dev(X)
