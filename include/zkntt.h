@@ -91,15 +91,20 @@ typedef struct {
  * (the transform of Section II-B; the coset form of Fig. 2).
  *   out          receives the plan handle (not written on failure)
  *   field        ZKNTT_BLS12_381_FR, ZKNTT_BN254_FR or ZKNTT_BLS12_377_FR
- *   log_n        1 .. 28 for every field (device-memory bound; the fields'
- *                2-adicities are 32, 28 and 47)
+ *   log_n        1 .. the field's 2-adicity (32, 28 and 47); above 32 the
+ *                vector and its scratch (2 x 2^log_n x 32 bytes, 512 GiB at
+ *                2^33) exceed any device's memory: ZKNTT_ENOMEM
  *   dir          ZKNTT_FORWARD or ZKNTT_INVERSE
  *   coset_shift  NULL for a plain transform, else the shift g as 8 uint32
  *                Montgomery-form limbs (host memory, read during the call);
  *                must be nonzero and canonical.
  * The plan owns its device twiddle tables (allocated and filled here, freed by
- * zkntt_plan_destroy).  Returns EINVAL on bad arguments, ENOMEM when the tables
- * do not fit, ECUDA on other CUDA failures.
+ * zkntt_plan_destroy).  Without a tuned schedule or an explicit mode, the
+ * inter-pass twiddles are precomputed tables (n entries for the first pass)
+ * when those fit beside three vectors in the device memory free at creation,
+ * else formed on the fly from split-exponent tables of about 2 sqrt(n)
+ * entries.  Returns EINVAL on bad arguments, ENOMEM when the tables do not
+ * fit, ECUDA on other CUDA failures.
  */
 zkntt_status zkntt_plan_create(zkntt_plan *out, zkntt_field field, int log_n, zkntt_dir dir,
                                const uint32_t *coset_shift);
@@ -329,6 +334,18 @@ zkntt_status zkntt_field_info(zkntt_field field, uint32_t modulus[8], uint32_t g
 zkntt_status zkntt_field_op(zkntt_field field, int op, const void *d_a, const void *d_b, void *d_c,
                             size_t n, void *stream);
 
+/* Scale by a geometric sequence: d_out[i] = d_x[i] * c * base^i for i < n
+ * (c and base: 8 Montgomery limbs in host memory, canonical; in place
+ * allowed).  This is the twiddle step of the four-step decomposition of the
+ * transform (Section II-B: a block NTT is bounded by shared memory, so large
+ * transforms are split into sub-transforms joined by twiddle factors), used
+ * when the sub-transforms run on different GPUs; with base = 1 it multiplies
+ * by the constant c.  Tables of about 2 sqrt(n) powers come from the
+ * library's stream-ordered pool for the call.  Non-canonical c or base,
+ * null or misaligned pointers, partial overlap -> ZKNTT_EINVAL. */
+zkntt_status zkntt_scale_powers(zkntt_field field, const void *d_x, void *d_out, size_t n,
+                                const uint32_t *c_mont, const uint32_t *base_mont, void *stream);
+
 /* Groth16 pointwise step on its own (the (A B - C) / Z step of Fig. 2):
  * d_h_i = (a_i b_i - c_i) * z, z given as 8 Montgomery limbs in host memory. */
 zkntt_status zkntt_pointwise(zkntt_field field, const void *d_a, const void *d_b, const void *d_c,
@@ -371,13 +388,18 @@ zkntt_status zkntt_mulbench(zkntt_field field, int blocks, int threads, int iter
 /*
  * Peak calibration of the 32-bit integer multiply-add (IMAD) rate, the
  * denominator of the transform's roofline (Sections IV-B and IV-C find FF_mul
- * bound by the INT32 pipe and weight IMAD in its integer roofline): a grid of
- * `blocks` x `threads` (32..1024) runs `iters` steps of eight independent
- * register-resident chains per thread, of mad.lo.u32 (mode 0: one 32-bit
- * multiply-add) or mad.wide.u32 (mode 1: a 32 x 32 -> 64 multiply-add), and
- * writes one checksum word per thread to d_sink.  8 * iters multiply-adds per
- * thread; time it with CUDA events on `stream`.  mode outside 0..1 or bad
- * sizes -> ZKNTT_EINVAL.
+ * bound by the INT32 pipe and weight IMAD in its integer roofline), and of the
+ * multiply forms a Montgomery product is built from: a grid of `blocks` x
+ * `threads` (32..1024) runs `iters` steps of eight independent
+ * register-resident chains per thread and writes one checksum word per thread
+ * to d_sink.  One step is, by mode:
+ *   0  mad.lo.u32     (one 32-bit multiply-add: the peak rate)
+ *   1  mad.wide.u32   (32 x 32 -> 64 multiply with a 64-bit addend)
+ *   2  mul.wide.u32   (32 x 32 -> 64 multiply, no addend)
+ *   3  mad.hi.u32     (high half of a 32 x 32 product plus an addend)
+ *   4  mad.lo.cc.u32 + madc.hi.u32 (a carry-chained pair: two instructions)
+ * 8 * iters steps per thread; time it with CUDA events on `stream`.  mode
+ * outside 0..4 or bad sizes -> ZKNTT_EINVAL.
  */
 zkntt_status zkntt_imadbench(int mode, int blocks, int threads, int iters, void *d_sink,
                              void *stream);

@@ -17,7 +17,7 @@ from ._native import ZkNttError, FIELDS, TWIDDLE_MODES
 
 __all__ = ["Plan", "ZkNttError", "FIELDS", "execute_batch", "execute_batch_signal",
            "CompletionFlags", "groth16_h", "Groth16Graph", "field_info",
-           "field_op", "pointwise", "tune", "sync_status", "mulbench", "imadbench", "pool_info",
+           "field_op", "pointwise", "scale_powers", "tune", "sync_status", "mulbench", "imadbench", "pool_info",
            "new_vector"]
 
 
@@ -303,6 +303,16 @@ def field_op(field, op: str, a, b, out=None, stream=None) -> torch.Tensor:
     out = torch.empty_like(a) if out is None else out
     N.check(N.lib().zkntt_field_op(_field_id(field), ops[op], _ptr(a), _ptr(b), _ptr(out),
                                    a.numel() // 8, _stream_handle(stream)), "zkntt_field_op")
+    return out
+
+
+def scale_powers(field, x, c_mont: int, base_mont: int, out=None, stream=None) -> torch.Tensor:
+    """out[i] = x[i] * c * base^i (Montgomery-form c and base; in place when
+    out is x)."""
+    out = torch.empty_like(x) if out is None else out
+    N.check(N.lib().zkntt_scale_powers(_field_id(field), _ptr(x), _ptr(out), x.numel() // 8,
+                                       N.limbs_of(c_mont), N.limbs_of(base_mont),
+                                       _stream_handle(stream)), "zkntt_scale_powers")
     return out
 
 

@@ -80,6 +80,7 @@ SIGNATURES = {
     "zkntt_imadbench": [_i, _i, _i, _i, _vp, _vp],
     "zkntt_selftest_device_check": [ctypes.POINTER(_i), ctypes.POINTER(_i)],
     "zkntt_pool_info": [ctypes.POINTER(_sz), ctypes.POINTER(_sz)],
+    "zkntt_scale_powers": [_i, _vp, _vp, _sz, _u32p, _u32p, _vp],
 }
 
 

@@ -53,6 +53,23 @@ __global__ void gen_twiddle_kernel(uint4 *out, uint32_t K, uint32_t lo_bits, con
     }
 }
 
+// out[i] = x[i] * hi[i >> split] * lo[i & (2^split - 1)]: with lo[t] = c base^t
+// and hi[u] = base^(u 2^split) this is x[i] * c * base^i
+template <class F>
+__global__ void scale_powers_kernel(const uint4 *x, uint4 *out, size_t n, const uint4 *hi,
+                                    const uint4 *lo, uint32_t split) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += size_t(gridDim.x) * blockDim.x) {
+        uint32_t v[8], a[8], b[8];
+        ldg_elem(a, hi + 2 * (i >> split));
+        ldg_elem(b, lo + 2 * (i & ((size_t(1) << split) - 1)));
+        mul<F>(a, a, b);
+        ldg_elem(v, x + 2 * i);
+        mul<F>(v, a, v);
+        st_elem(out + 2 * i, v);
+    }
+}
+
 // c = op(a, b) elementwise: 0 mul, 1 add, 2 sub
 template <class F>
 __global__ void field_op_kernel(int op, const uint4 *a, const uint4 *b, uint4 *c, size_t n) {

@@ -91,38 +91,76 @@ __global__ void __launch_bounds__(BATCH_THREADS, BATCH_MIN_BLOCKS)
 }
 
 // Calibration of the 32-bit integer multiply-add rate (the peak the transform's
-// roofline is quoted against): every thread runs eight independent chains of
-// mode 0: mad.lo.u32 (x = x * y + z, low 32 bits), or
-// mode 1: mad.wide.u32 (64-bit x = lo(x) * y + x, a 32 x 32 -> 64 multiply-add).
-// The operands live in registers and each chain's next step depends on its
-// previous one, so nothing can be folded away; a checksum per thread keeps the
-// chains live.  Count: 8 * iters multiply-adds per thread.
+// roofline is quoted against) and of the multiply forms a Montgomery product
+// is built from.  Every thread runs eight independent register chains of
+//   mode 0: mad.lo.u32   x = lo(x * y) + z
+//   mode 1: mad.wide.u32 x = lo(x) * y + x               (64-bit addend)
+//   mode 2: mul.wide.u32 x = lo(x) * y                    (no addend)
+//   mode 3: mad.hi.u32   x = hi(x * y) + z
+//   mode 4: mad.lo.cc.u32 / madc.hi.u32 pair (x, c) = (lo(x y) + z, hi(x y) + carry):
+//           two instructions per step
+// Each chain's next step depends on its previous one, so nothing can be
+// folded away; a checksum per thread keeps the chains live.  Count: 8 * iters
+// steps per thread (16 * iters instructions in mode 4).
 __global__ void __launch_bounds__(1024) imadbench_kernel(int mode, int iters, uint32_t *sink) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t y = tid * 0x9E3779B9u + 0x7f4a7c15u, z = tid ^ 0x85ebca6bu;
     uint32_t acc = 0;
-    if (mode == 0) {
+    if (mode == 0 || mode == 3) {
         uint32_t x[8];
 #pragma unroll
         for (int k = 0; k < 8; k++) x[k] = tid + 0x1000193u * k;
-        for (int it = 0; it < iters; it++) {
+        if (mode == 0) {
+            for (int it = 0; it < iters; it++) {
 #pragma unroll
-            for (int k = 0; k < 8; k++)
-                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[k]) : "r"(y), "r"(z));
+                for (int k = 0; k < 8; k++)
+                    asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[k]) : "r"(y), "r"(z));
+            }
+        } else {
+            for (int it = 0; it < iters; it++) {
+#pragma unroll
+                for (int k = 0; k < 8; k++)
+                    asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(x[k]) : "r"(y), "r"(z));
+            }
         }
 #pragma unroll
         for (int k = 0; k < 8; k++) acc ^= x[k];
-    } else {
+    } else if (mode == 1 || mode == 2) {
         uint64_t x[8];
 #pragma unroll
         for (int k = 0; k < 8; k++) x[k] = tid + 0x1000193ull * k;
-        for (int it = 0; it < iters; it++) {
+        if (mode == 1) {
+            for (int it = 0; it < iters; it++) {
 #pragma unroll
-            for (int k = 0; k < 8; k++)
-                asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(x[k]) : "r"(uint32_t(x[k])), "r"(y));
+                for (int k = 0; k < 8; k++)
+                    asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(x[k]) : "r"(uint32_t(x[k])), "r"(y));
+            }
+        } else {
+            for (int it = 0; it < iters; it++) {
+#pragma unroll
+                for (int k = 0; k < 8; k++)
+                    asm volatile("mul.wide.u32 %0, %1, %2;" : "=l"(x[k]) : "r"(uint32_t(x[k]) ^ uint32_t(x[k] >> 32)), "r"(y));
+            }
         }
 #pragma unroll
         for (int k = 0; k < 8; k++) acc ^= uint32_t(x[k]) ^ uint32_t(x[k] >> 32);
+    } else {
+        uint32_t x[8], c[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            x[k] = tid + 0x1000193u * k;
+            c[k] = 0;
+        }
+        for (int it = 0; it < iters; it++) {
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                asm volatile("mad.lo.cc.u32 %0, %0, %2, %3;\n\t"
+                             "madc.hi.u32 %1, %0, %2, %1;"
+                             : "+r"(x[k]), "+r"(c[k])
+                             : "r"(y), "r"(z));
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) acc ^= x[k] ^ c[k];
     }
     sink[tid] = acc;
 }

@@ -15,6 +15,7 @@ struct FieldKernels {
     const void *field_op;
     const void *pointwise;
     const void *mulbench;
+    const void *scale_powers;
 };
 
 const FieldKernels &kernels_bls12_381();

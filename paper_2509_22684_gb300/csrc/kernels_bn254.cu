@@ -16,6 +16,7 @@ const FieldKernels &kernels_bn254() {
         (const void *)&field_op_kernel<F>,
         (const void *)&pointwise_kernel<F>,
         (const void *)&mulbench_kernel<F>,
+        (const void *)&scale_powers_kernel<F>,
     };
     return k;
 }

@@ -142,7 +142,9 @@ __device__ __forceinline__ bool out_factor(uint32_t f[8], const PassArgs &a, uin
         ldg_elem(f, a.tw + 2 * ((size_t(d) << a.lo_bits) + lo));
         return true;
     }
-    const uint32_t e = (lo * brev_bits(d, a.K)) & ((1u << a.tw_bits) - 1u);
+    // lo < 2^lo_bits and rev(d) < 2^K, so e < 2^tw_bits = n_i: no reduction
+    // (and no overflow: tw_bits <= 32)
+    const uint32_t e = lo * brev_bits(d, a.K);
     uint32_t g[8];
     ldg_elem(f, a.w_hi + 2 * size_t(e >> a.split_bits));
     ldg_elem(g, a.w_lo + 2 * size_t(e & ((1u << a.split_bits) - 1u)));
@@ -218,6 +220,9 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
         const uint32_t lh = K - 1 - s;
         const uint32_t h = 1u << lh;
         const uint4 *ws = a.w_stage + 2 * size_t(N - 2 * h);
+        // slot of row i0 + h from that of row i0 (bit lh of i0 is clear): the
+        // swizzle term changes only when lh = 3
+        const uint32_t step = K < 3 ? h : (h ^ (lh == 3 ? 7u : 0u));
         if constexpr (ILP == 0) {
             // software-pipelined: the product of one butterfly overlaps the
             // loads and add/subtract of the next (every thread owns >= 2)
@@ -229,7 +234,7 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
                 const uint32_t j = b & (h - 1);
                 const uint32_t i0 = ((b >> lh) << (lh + 1)) | j;
                 q0 = smem_slot(cc, i0, K, lc);
-                q1 = smem_slot(cc, i0 + h, K, lc);
+                q1 = q0 ^ step;
                 uint32_t py[8];
                 lds_elem(px, s_lo, s_hi, q0);
                 lds_elem(py, s_lo, s_hi, q1);
@@ -267,7 +272,7 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
                 const uint32_t j = b & (h - 1);
                 const uint32_t i0 = ((b >> lh) << (lh + 1)) | j;
                 s0[k] = smem_slot(cc, i0, K, lc);
-                s1[k] = smem_slot(cc, i0 + h, K, lc);
+                s1[k] = s0[k] ^ step;
                 lds_elem(x[k], s_lo, s_hi, s0[k]);
                 lds_elem(y[k], s_lo, s_hi, s1[k]);
                 ldg_elem(w[k], ws + 2 * size_t(j));

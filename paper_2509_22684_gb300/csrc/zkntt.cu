@@ -488,9 +488,24 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
         if (opts->ilp < 1 || opts->ilp > NUM_VARIANTS) return ZKNTT_EINVAL;
         ilp = opts->ilp;
     }
+    const int p = P->passes;
+    if (mode == ZKNTT_TWIDDLE_AUTO && p > 1) {
+        // Precomputed inter-pass tables (pass i: 2^(K_i + lo_bits_i) entries;
+        // pass 1's is n entries) unless they would not fit beside the input,
+        // output and scratch vectors in the device memory free now: then the
+        // split-exponent tables (about 2 sqrt(n_i) entries) instead.
+        size_t fr = 0, tot = 0;
+        ZK_CHECK(cudaMemGetInfo(&fr, &tot));
+        size_t tables = 0;
+        for (int i = 0, hb = 0; i < p - 1; i++) {
+            hb += k[i];
+            tables += size_t(32) << (L - hb + k[i]);
+        }
+        const size_t vectors = 3 * (size_t(32) << L);
+        if (tables + vectors > fr) mode = ZKNTT_TWIDDLE_OTF;
+    }
     if (mode != ZKNTT_TWIDDLE_OTF) mode = ZKNTT_TWIDDLE_PRECOMP;
     P->mode = mode;
-    const int p = P->passes;
 
     // ---- scalars
     E8 w = hpow(F, F.wmax, uint64_t(1) << (F.s - L));  // w_n
@@ -710,7 +725,10 @@ zkntt_status create_plan(zkntt_plan *out, zkntt_field field, int log_n, zkntt_di
     if (!valid_field(field)) return ZKNTT_EINVAL;
     if (dir != ZKNTT_FORWARD && dir != ZKNTT_INVERSE) return ZKNTT_EINVAL;
     const HostField &F = host_field(field);
-    if (log_n < 1 || log_n > std::min(F.s, 28)) return ZKNTT_EINVAL;
+    if (log_n < 1 || log_n > F.s) return ZKNTT_EINVAL;
+    // A transform of 2^33 or more elements needs at least 2 x 2^33 x 32 bytes
+    // (the vector and its scratch, 512 GiB): more than any device holds.
+    if (log_n > 32) return ZKNTT_ENOMEM;
     if (opts && (opts->twiddle_mode < 0 || opts->twiddle_mode > 2)) return ZKNTT_EINVAL;
     zkntt_plan_s *P = new (std::nothrow) zkntt_plan_s;
     if (!P) return ZKNTT_ENOMEM;
@@ -1490,6 +1508,46 @@ zkntt_status zkntt_selftest_device_check(int *checked, int *rejected) {
     return st;
 }
 
+zkntt_status zkntt_scale_powers(zkntt_field field, const void *d_x, void *d_out, size_t n,
+                                const uint32_t *c_mont, const uint32_t *base_mont, void *stream) {
+    if (!valid_field(field) || !c_mont || !base_mont) return ZKNTT_EINVAL;
+    if (n == 0) return ZKNTT_OK;
+    if (bad_ptr(d_x) || bad_ptr(d_out)) return ZKNTT_EINVAL;
+    if (partial_overlap(d_x, d_out, n * 32)) return ZKNTT_EINVAL;
+    const HostField &F = host_field(field);
+    E8 c, base;
+    for (int i = 0; i < 8; i++) {
+        c[i] = c_mont[i];
+        base[i] = base_mont[i];
+    }
+    if (geq8(c, F.p) || geq8(base, F.p)) return ZKNTT_EINVAL;
+    DeviceInfo *dev;
+    zkntt_status st = device_info(&dev);
+    if (st != ZKNTT_OK) return st;
+    int bits = 0;
+    while ((size_t(1) << bits) < n) bits++;
+    const int sp = (bits + 1) / 2;
+    // lo[t] = c base^t (t < 2^sp), hi[u] = base^(u 2^sp) (u < 2^(bits - sp))
+    std::vector<E8> tab = powers(F, base, size_t(1) << sp, c);
+    const std::vector<E8> hi = powers(F, hpow(F, base, uint64_t(1) << sp), size_t(1) << (bits - sp), F.one);
+    tab.insert(tab.end(), hi.begin(), hi.end());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint4 *d_tab = nullptr;
+    st = pool_alloc(reinterpret_cast<void **>(&d_tab), tab.size() * 32, s);
+    if (st != ZKNTT_OK) return st;
+    // pageable source: the copy is staged before the call returns
+    st = from_cuda(cudaMemcpyAsync(d_tab, tab.data(), tab.size() * 32, cudaMemcpyHostToDevice, s));
+    if (st == ZKNTT_OK) {
+        const uint4 *lo_t = d_tab, *hi_t = d_tab + 2 * (size_t(1) << sp);
+        uint32_t usp = uint32_t(sp);
+        void *args[] = {&d_x, &d_out, &n, &hi_t, &lo_t, &usp};
+        st = from_cuda(cudaLaunchKernel(field_kernels(field).scale_powers,
+                                        dim3(grid_for(n, 256, dev->sms)), dim3(256), args, 0, s));
+    }
+    zkntt_status st2 = from_cuda(cudaFreeAsync(d_tab, s));
+    return st != ZKNTT_OK ? st : st2;
+}
+
 zkntt_status zkntt_pool_info(size_t *reserved_bytes, size_t *used_bytes) {
     if (!reserved_bytes || !used_bytes) return ZKNTT_EINVAL;
     DeviceInfo *dev;
@@ -1505,7 +1563,7 @@ zkntt_status zkntt_pool_info(size_t *reserved_bytes, size_t *used_bytes) {
 
 zkntt_status zkntt_imadbench(int mode, int blocks, int threads, int iters, void *d_sink,
                              void *stream) {
-    if (mode < 0 || mode > 1) return ZKNTT_EINVAL;
+    if (mode < 0 || mode > 4) return ZKNTT_EINVAL;
     if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !d_sink) return ZKNTT_EINVAL;
     void *args[] = {&mode, &iters, &d_sink};
     return from_cuda(cudaLaunchKernel(imadbench_kernel_ptr(), dim3(blocks), dim3(threads), args, 0,

@@ -53,7 +53,8 @@ def test_host_side_validation_without_gpu(lib):
     # field, log_n, direction and null handle are rejected before any CUDA call
     assert lib.zkntt_plan_create(ctypes.byref(h), 7, 10, 0, None) == N.EINVAL
     assert lib.zkntt_plan_create(ctypes.byref(h), 3, 10, 0, None) == N.EINVAL
-    assert lib.zkntt_plan_create(ctypes.byref(h), 2, 29, 0, None) == N.EINVAL
+    assert lib.zkntt_plan_create(ctypes.byref(h), 2, 48, 0, None) == N.EINVAL   # above 2-adicity 47
+    assert lib.zkntt_plan_create(ctypes.byref(h), 2, 33, 0, None) == N.ENOMEM   # 2^33: no device holds it
     assert lib.zkntt_plan_create(ctypes.byref(h), 0, 0, 0, None) == N.EINVAL
     assert lib.zkntt_plan_create(ctypes.byref(h), 1, 29, 0, None) == N.EINVAL
     assert lib.zkntt_plan_create(ctypes.byref(h), 0, 33, 0, None) == N.EINVAL
@@ -73,9 +74,13 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.zkntt_selftest_timeout(0, None) == N.EINVAL
     assert lib.zkntt_inject_timeout(0, None) == N.EINVAL
     assert lib.zkntt_inject_timeout(10001, None) == N.EINVAL
-    assert lib.zkntt_imadbench(2, 1, 32, 1, ctypes.c_void_p(256), None) == N.EINVAL
+    assert lib.zkntt_imadbench(5, 1, 32, 1, ctypes.c_void_p(256), None) == N.EINVAL
     assert lib.zkntt_imadbench(0, 1, 32, 1, None, None) == N.EINVAL
     assert lib.zkntt_selftest_device_check(None, None) == N.EINVAL
+    one = N.u32_array([1] + [0] * 7)
+    assert lib.zkntt_scale_powers(0, None, None, 4, None, one, None) == N.EINVAL
+    assert lib.zkntt_scale_powers(9, None, None, 4, one, one, None) == N.EINVAL
+    assert lib.zkntt_scale_powers(0, None, None, 0, one, one, None) == N.OK    # empty: no-op
 
 
 def test_field_info_without_gpu(lib):

@@ -272,3 +272,31 @@ def test_execute_host_buffered_matches_device_execution(F):
         assert np.array_equal(yh.numpy().view(np.uint32).reshape(-1, 8), want)
         with pytest.raises(ZkNttError):
             p.execute_host_buffered(xh, yh, work[:8 * (1 << L)], stream=s)
+
+
+def test_bls12_381_2_30_beyond_the_tuned_sizes():
+    """2^30 BLS12-381 F_r (32 GiB per vector; sizes above 2^28 run with the
+    planner's default split and pick their twiddle mode by free memory):
+    outputs at sampled k against the definition (Horner in the C oracle), and
+    inverse(forward(x)) == x over the whole vector, compared on the device."""
+    import torch
+    from workloads import uniform_elements_threaded
+    F = fld.BLS12_381
+    L = 30
+    X = uniform_elements_threaded(F.r, 1 << L, 2030)
+    x = to_dev(X)
+    with _plan(F, L, "ntt") as p:
+        assert p.describe()["passes"] == 3
+        y = p.execute(x)
+        torch.cuda.synchronize()
+    w = F.root(L)
+    for k in (1, (1 << L) - 1, 987654321):
+        got = int.from_bytes(to_host(y[k:k + 1]).tobytes(), "little")
+        assert got == cpu.eval_at(F, X, F.to_mont(pow(w, k, F.r))), k
+    del X
+    with _plan(F, L, "intt") as q:
+        q.execute(y, y)
+        torch.cuda.synchronize()
+    assert torch.equal(y, x)
+    del x, y
+    torch.cuda.empty_cache()

@@ -42,3 +42,16 @@ def test_batch_and_trace_are_deterministic():
     t = poisson_trace(5000, 200, 100.0)
     assert all(t[i].arrival_s < t[i + 1].arrival_s for i in range(len(t) - 1))
     assert {q.log_n for q in t} <= set(range(12, 25))
+
+
+def test_threaded_generator_equals_the_sequential_one():
+    """uniform_elements_threaded draws exactly uniform_elements' values, for
+    block sizes that split the candidates many ways (including blocks smaller
+    than one accepted value's share and a wave that ends mid-block)."""
+    from workloads import uniform_elements_threaded
+    for F in (fld.BLS12_381, fld.BN254):
+        for n, block, threads in ((0, 8, 2), (1, 1, 3), (1000, 7, 4), (20000, 512, 5),
+                                  (100000, 1 << 14, 16)):
+            want = uniform_elements(F.r, n, 91)
+            got = uniform_elements_threaded(F.r, n, 91, threads=threads, block=block)
+            assert got.shape == (n, 8) and np.array_equal(got, want), (F.name, n, block)

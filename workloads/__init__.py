@@ -96,6 +96,53 @@ def uniform_elements(modulus: int, n: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(out).view(np.uint32).reshape(n, 8)
 
 
+def _accepted_block(modulus: int, seed: int, cand0: int, count: int) -> np.ndarray:
+    """Accepted values among candidates cand0 .. cand0+count-1, in order, as
+    [k, 4] uint64 words (the candidate rule of ``uniform_elements``)."""
+    bits = modulus.bit_length()
+    top_bits = bits - 192
+    top_mask = np.uint64((1 << top_bits) - 1) if top_bits < 64 else np.uint64(_MASK64)
+    mw = _words_of(modulus)
+    w = splitmix64(seed, 4 * cand0, 4 * count).reshape(count, 4)
+    w[:, 3] &= top_mask
+    less = np.zeros(count, dtype=bool)
+    eq = np.ones(count, dtype=bool)
+    for k in (3, 2, 1, 0):
+        mk = np.uint64(mw[k])
+        less |= eq & (w[:, k] < mk)
+        eq &= w[:, k] == mk
+    return w[less]
+
+
+def uniform_elements_threaded(modulus: int, n: int, seed: int, threads: int | None = None,
+                              block: int = 1 << 20) -> np.ndarray:
+    """The same values as ``uniform_elements(modulus, n, seed)``, drawn by
+    several threads at once (for vectors of 2^26 elements and more): the
+    candidates are cut into consecutive blocks of ``block`` candidates, each
+    thread filters whole blocks, and the accepted values are concatenated in
+    candidate order until n are taken."""
+    import concurrent.futures as cf
+    import os
+    if modulus <= 1 or modulus.bit_length() > 256:
+        raise ValueError("modulus must be in (1, 2^256)")
+    threads = threads or min(16, os.cpu_count() or 1)
+    out = np.empty((n, 4), dtype=np.uint64)
+    filled, nxt = 0, 0
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        while filled < n:
+            wave = [ex.submit(_accepted_block, modulus, seed, (nxt + i) * block, block)
+                    for i in range(threads)]
+            nxt += threads
+            for f in wave:
+                acc = f.result()
+                take = min(n - filled, acc.shape[0])
+                out[filled:filled + take] = acc[:take]
+                filled += take
+                if filled == n:
+                    break
+    return out.view(np.uint32).reshape(n, 8)
+
+
 def uniform_elements_scalar(modulus: int, n: int, seed: int) -> list[int]:
     """Plain-Python statement of ``uniform_elements`` (for tests), as ints."""
     bits = modulus.bit_length()
