@@ -82,8 +82,11 @@ typedef struct {
                               per SM), 2 = two interleaved butterflies (2 blocks), 3 = one
                               butterfly with registers for 4 blocks, 4 = software-pipelined
                               stage loop (2 blocks), 5 = as 3 with twice the threads per
-                              tile (for small transforms); 0 = auto; outside 0..5 ->
-                              ZKNTT_EINVAL */
+                              tile (for small transforms), 6 = as 3 with two tile
+                              buffers (the next tile's loads overlap this tile's
+                              arithmetic), 7 = as 1 with the stages of pair distance
+                              16, 8 and 4 exchanged by warp shuffles instead of shared
+                              memory; 0 = auto; outside 0..7 -> ZKNTT_EINVAL */
 } zkntt_plan_options;
 
 /*

@@ -298,6 +298,184 @@ __device__ __forceinline__ void merge_reduce(uint32_t t[9], const uint64_t Q[8])
 #define ZKNTT_MUL_FORM 0
 #endif
 
+// ---------------------------------------------------------------------------
+// Form 3 (build-time option, not the default): one level of Karatsuba for the
+// 256 x 256-bit product, then a separated-operand-scanning reduction.  The
+// paper suggests trading IMAD for IADD3-class work (Section IV-B-2); with
+// a = aL + 2^128 aH and b = bL + 2^128 bH the product takes three 4 x 4 limb
+// products (48 wide multiplies instead of 64):
+//   a b = LL + 2^128 (M - LL - HH) + 2^256 HH,
+//   LL = aL bL, HH = aH bH, M = (aL + aH)(bL + bH),
+// where the sums carry one bit each, corrected by masked adds.
+
+// z = x * y for 4-limb x, y (8 limbs)
+__device__ __forceinline__ void mul4x4(uint32_t z[8], const uint32_t x[4], const uint32_t y[4]) {
+    uint64_t P[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) P[j] = uint64_t(x[j]) * y[0];
+    z[0] = uint32_t(P[0]);
+    asm("add.cc.u32  %0, %4, %5;\n\t"
+        "addc.cc.u32 %1, %6, %7;\n\t"
+        "addc.cc.u32 %2, %8, %9;\n\t"
+        "addc.u32    %3, %10, 0;"
+        : "=r"(z[1]), "=r"(z[2]), "=r"(z[3]), "=r"(z[4])
+        : "r"(uint32_t(P[0] >> 32)), "r"(uint32_t(P[1])), "r"(uint32_t(P[1] >> 32)),
+          "r"(uint32_t(P[2])), "r"(uint32_t(P[2] >> 32)), "r"(uint32_t(P[3])),
+          "r"(uint32_t(P[3] >> 32)));
+#pragma unroll
+    for (int i = 1; i < 4; i++) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) P[j] = uint64_t(x[j]) * y[i];
+        uint32_t top;
+        asm("add.cc.u32  %0, %0, %5;\n\t"
+            "addc.cc.u32 %1, %1, %6;\n\t"
+            "addc.cc.u32 %2, %2, %7;\n\t"
+            "addc.cc.u32 %3, %3, %8;\n\t"
+            "addc.u32    %4, 0, 0;\n\t"
+            "add.cc.u32  %1, %1, %9;\n\t"
+            "addc.cc.u32 %2, %2, %10;\n\t"
+            "addc.cc.u32 %3, %3, %11;\n\t"
+            "addc.u32    %4, %4, %12;"
+            : "+r"(z[i]), "+r"(z[i + 1]), "+r"(z[i + 2]), "+r"(z[i + 3]), "=r"(top)
+            : "r"(uint32_t(P[0])), "r"(uint32_t(P[1])), "r"(uint32_t(P[2])), "r"(uint32_t(P[3])),
+              "r"(uint32_t(P[0] >> 32)), "r"(uint32_t(P[1] >> 32)), "r"(uint32_t(P[2] >> 32)),
+              "r"(uint32_t(P[3] >> 32)));
+        z[i + 4] = top;
+    }
+}
+
+
+// Form 3's product: T = a b (16 limbs) by one Karatsuba level, then eight
+// word reductions T <- (T + m r 2^(32 i)) with m = T_i r' mod 2^32; the carry
+// out of each row's top limb is added to the next row's top limb.  a must be
+// canonical (so aH < 2^127), b may be any value below 2^256; T < r 2^256, so
+// the result is below 2r and one conditional subtraction canonicalises it.
+template <class F>
+__device__ __forceinline__ void mul_karatsuba(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
+    const uint32_t P[8] = {F::P0, F::P1, F::P2, F::P3, F::P4, F::P5, F::P6, F::P7};
+    uint32_t LL[8], HH[8], M[9], sa[4], sb[4], ca, cb;
+    mul4x4(LL, a, b);
+    mul4x4(HH, a + 4, b + 4);
+    asm("add.cc.u32  %0, %5, %9;\n\t"
+        "addc.cc.u32 %1, %6, %10;\n\t"
+        "addc.cc.u32 %2, %7, %11;\n\t"
+        "addc.cc.u32 %3, %8, %12;\n\t"
+        "addc.u32    %4, 0, 0;"
+        : "=r"(sa[0]), "=r"(sa[1]), "=r"(sa[2]), "=r"(sa[3]), "=r"(ca)
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]));
+    asm("add.cc.u32  %0, %5, %9;\n\t"
+        "addc.cc.u32 %1, %6, %10;\n\t"
+        "addc.cc.u32 %2, %7, %11;\n\t"
+        "addc.cc.u32 %3, %8, %12;\n\t"
+        "addc.u32    %4, 0, 0;"
+        : "=r"(sb[0]), "=r"(sb[1]), "=r"(sb[2]), "=r"(sb[3]), "=r"(cb)
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
+    mul4x4(M, sa, sb);
+    // M += 2^128 (ca sb + cb sa) + 2^256 ca cb
+    const uint32_t ma = 0u - ca, mb = 0u - cb;
+    asm("add.cc.u32  %0, %0, %5;\n\t"
+        "addc.cc.u32 %1, %1, %6;\n\t"
+        "addc.cc.u32 %2, %2, %7;\n\t"
+        "addc.cc.u32 %3, %3, %8;\n\t"
+        "addc.u32    %4, 0, 0;\n\t"
+        "add.cc.u32  %0, %0, %9;\n\t"
+        "addc.cc.u32 %1, %1, %10;\n\t"
+        "addc.cc.u32 %2, %2, %11;\n\t"
+        "addc.cc.u32 %3, %3, %12;\n\t"
+        "addc.u32    %4, %4, %13;"
+        : "+r"(M[4]), "+r"(M[5]), "+r"(M[6]), "+r"(M[7]), "=r"(M[8])
+        : "r"(sb[0] & ma), "r"(sb[1] & ma), "r"(sb[2] & ma), "r"(sb[3] & ma),
+          "r"(sa[0] & mb), "r"(sa[1] & mb), "r"(sa[2] & mb), "r"(sa[3] & mb), "r"(ca & cb));
+    // M -= LL, M -= HH (the middle term aL bH + aH bL >= 0)
+    asm("sub.cc.u32  %0, %0, %9;\n\t"
+        "subc.cc.u32 %1, %1, %10;\n\t"
+        "subc.cc.u32 %2, %2, %11;\n\t"
+        "subc.cc.u32 %3, %3, %12;\n\t"
+        "subc.cc.u32 %4, %4, %13;\n\t"
+        "subc.cc.u32 %5, %5, %14;\n\t"
+        "subc.cc.u32 %6, %6, %15;\n\t"
+        "subc.cc.u32 %7, %7, %16;\n\t"
+        "subc.u32    %8, %8, 0;\n\t"
+        "sub.cc.u32  %0, %0, %17;\n\t"
+        "subc.cc.u32 %1, %1, %18;\n\t"
+        "subc.cc.u32 %2, %2, %19;\n\t"
+        "subc.cc.u32 %3, %3, %20;\n\t"
+        "subc.cc.u32 %4, %4, %21;\n\t"
+        "subc.cc.u32 %5, %5, %22;\n\t"
+        "subc.cc.u32 %6, %6, %23;\n\t"
+        "subc.cc.u32 %7, %7, %24;\n\t"
+        "subc.u32    %8, %8, 0;"
+        : "+r"(M[0]), "+r"(M[1]), "+r"(M[2]), "+r"(M[3]), "+r"(M[4]), "+r"(M[5]), "+r"(M[6]),
+          "+r"(M[7]), "+r"(M[8])
+        : "r"(LL[0]), "r"(LL[1]), "r"(LL[2]), "r"(LL[3]), "r"(LL[4]), "r"(LL[5]), "r"(LL[6]),
+          "r"(LL[7]), "r"(HH[0]), "r"(HH[1]), "r"(HH[2]), "r"(HH[3]), "r"(HH[4]), "r"(HH[5]),
+          "r"(HH[6]), "r"(HH[7]));
+    // T = LL + 2^128 M + 2^256 HH
+    uint32_t T[16];
+#pragma unroll
+    for (int i = 0; i < 4; i++) T[i] = LL[i];
+    asm("add.cc.u32  %0, %12, %20;\n\t"
+        "addc.cc.u32 %1, %13, %21;\n\t"
+        "addc.cc.u32 %2, %14, %22;\n\t"
+        "addc.cc.u32 %3, %15, %23;\n\t"
+        "addc.cc.u32 %4, %16, %24;\n\t"
+        "addc.cc.u32 %5, %17, %25;\n\t"
+        "addc.cc.u32 %6, %18, %26;\n\t"
+        "addc.cc.u32 %7, %19, %27;\n\t"
+        "addc.cc.u32 %8, %28, %29;\n\t"
+        "addc.cc.u32 %9, %30, 0;\n\t"
+        "addc.cc.u32 %10, %31, 0;\n\t"
+        "addc.u32    %11, %32, 0;"
+        : "=r"(T[4]), "=r"(T[5]), "=r"(T[6]), "=r"(T[7]), "=r"(T[8]), "=r"(T[9]), "=r"(T[10]),
+          "=r"(T[11]), "=r"(T[12]), "=r"(T[13]), "=r"(T[14]), "=r"(T[15])
+        : "r"(LL[4]), "r"(LL[5]), "r"(LL[6]), "r"(LL[7]), "r"(HH[0]), "r"(HH[1]), "r"(HH[2]),
+          "r"(HH[3]), "r"(M[0]), "r"(M[1]), "r"(M[2]), "r"(M[3]), "r"(M[4]), "r"(M[5]), "r"(M[6]),
+          "r"(M[7]), "r"(HH[4]), "r"(M[8]), "r"(HH[5]), "r"(HH[6]), "r"(HH[7]));
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        uint32_t m;
+        if constexpr (F::RP == 0xefffffffu) m = 0u - T[i] - (T[i] << 28);
+        else m = T[i] * F::RP;
+        uint64_t X[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) X[j] = uint64_t(m) * P[j] + T[i + j];
+        if constexpr (F::P0 == 0xf0000001u) {
+            uint32_t s0, cy;
+            asm("add.cc.u32 %0, %2, %3;\n\t"
+                "addc.u32   %1, 0, 0;"
+                : "=r"(s0), "=r"(cy)
+                : "r"(m), "r"(T[i]));
+            X[0] = uint64_t(m - (m >> 4) + cy) << 32;
+        }
+        uint32_t cn;
+        asm("add.cc.u32  %0, %9, %17;\n\t"
+            "addc.cc.u32 %1, %10, %18;\n\t"
+            "addc.cc.u32 %2, %11, %19;\n\t"
+            "addc.cc.u32 %3, %12, %20;\n\t"
+            "addc.cc.u32 %4, %13, %21;\n\t"
+            "addc.cc.u32 %5, %14, %22;\n\t"
+            "addc.cc.u32 %6, %15, %23;\n\t"
+            "addc.cc.u32 %7, %16, %7;\n\t"
+            "addc.u32    %8, 0, 0;\n\t"
+            "add.cc.u32  %7, %7, %24;\n\t"
+            "addc.u32    %8, %8, 0;"
+            : "=r"(T[i + 1]), "=r"(T[i + 2]), "=r"(T[i + 3]), "=r"(T[i + 4]), "=r"(T[i + 5]),
+              "=r"(T[i + 6]), "=r"(T[i + 7]), "+r"(T[i + 8]), "=r"(cn)
+            : "r"(uint32_t(X[0] >> 32)), "r"(uint32_t(X[1] >> 32)), "r"(uint32_t(X[2] >> 32)),
+              "r"(uint32_t(X[3] >> 32)), "r"(uint32_t(X[4] >> 32)), "r"(uint32_t(X[5] >> 32)),
+              "r"(uint32_t(X[6] >> 32)), "r"(uint32_t(X[7] >> 32)), "r"(uint32_t(X[1])),
+              "r"(uint32_t(X[2])), "r"(uint32_t(X[3])), "r"(uint32_t(X[4])), "r"(uint32_t(X[5])),
+              "r"(uint32_t(X[6])), "r"(uint32_t(X[7])), "r"(c));
+        c = cn;
+    }
+    uint32_t t[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) t[i] = T[8 + i];
+    reduce_once<F>(t);
+#pragma unroll
+    for (int i = 0; i < 8; i++) r[i] = t[i];
+}
 
 // r = a * b * 2^-256 mod p, canonical.  a must be canonical; b may be any
 // value below 2^256: with t <= 2r - 1, a <= r - 1 and b_i, m <= 2^32 - 1 an
@@ -306,6 +484,10 @@ __device__ __forceinline__ void merge_reduce(uint32_t t[9], const uint64_t Q[8])
 // canonicalises it.  r may alias a or b.
 template <class F>
 __device__ __forceinline__ void mul(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
+    if constexpr (ZKNTT_MUL_FORM == 3) {
+        mul_karatsuba<F>(r, a, b);
+        return;
+    }
     const uint32_t P[8] = {F::P0, F::P1, F::P2, F::P3, F::P4, F::P5, F::P6, F::P7};
     uint32_t bb[8];
 #pragma unroll

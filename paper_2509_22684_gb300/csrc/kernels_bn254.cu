@@ -10,7 +10,8 @@ const FieldKernels &kernels_bn254() {
     static const FieldKernels k = {
         {nullptr, (const void *)&ntt_pass_kernel<F, 1>, (const void *)&ntt_pass_kernel<F, 2>,
          (const void *)&ntt_pass_kernel<F, 3>, (const void *)&ntt_pass_kernel<F, 4>,
-         (const void *)&ntt_pass_kernel<F, 5>},
+         (const void *)&ntt_pass_kernel<F, 5>, (const void *)&ntt_pass_kernel<F, 6>,
+         (const void *)&ntt_pass_kernel<F, 7>},
         (const void *)&gen_powers_kernel<F>,
         (const void *)&gen_twiddle_kernel<F>,
         (const void *)&field_op_kernel<F>,

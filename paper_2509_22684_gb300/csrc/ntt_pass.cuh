@@ -92,6 +92,16 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// wait until at most N committed groups of this thread's copies are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void lds_elem(uint32_t x[8], const uint4 *s_lo, const uint4 *s_hi,
                                          uint32_t slot) {
     uint4 v0 = s_lo[slot], v1 = s_hi[slot];
@@ -160,9 +170,32 @@ __device__ __forceinline__ bool out_factor(uint32_t f[8], const PassArgs &a, uin
     return true;
 }
 
+// Issue (without waiting) the 16-byte copies of one tile into shared memory:
+// 8 lanes copy the low halves of 8 elements, the next 8 lanes their high
+// halves (tiles under 8 elements: element-major); columns fastest for strided
+// passes, rows fastest for the last.
+__device__ __forceinline__ void issue_tile_load(const PassArgs &a, uint4 *smem, uint32_t tile,
+                                                uint32_t nthreads) {
+    const uint32_t K = a.K, lc = a.log_cols;
+    const uint32_t N = 1u << K, C = 1u << lc, CN = C << K;
+    uint4 *s_lo = smem, *s_hi = smem + CN;
+    const uint32_t tid = threadIdx.x;
+    const bool grouped = CN >= 8;
+    for (uint32_t u = tid; tid < nthreads && u < 2 * CN; u += nthreads) {
+        const uint32_t e = grouped ? ((u & 7u) | ((u >> 4) << 3)) : (u >> 1);
+        const uint32_t half = grouped ? ((u >> 3) & 1u) : (u & 1u);
+        uint32_t d, cc;
+        if (a.last) { d = e & (N - 1); cc = e >> K; }
+        else        { cc = e & (C - 1); d = e >> lc; }
+        const size_t g = tile_src(a, tile, d, cc);
+        cp_async16((half ? s_hi : s_lo) + smem_slot(cc, d, K, lc), a.in + 2 * g + half);
+    }
+}
+
 // Process one tile with `nthreads` threads of the block (threads at or beyond
-// nthreads only take part in the barriers).
-template <class F, int ILP>
+// nthreads only take part in the barriers).  PRELOADED: the caller has
+// already copied the tile into `smem` and synchronised the block.
+template <class F, int ILP, bool PRELOADED = false, bool SHFL = false>
 __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_t tile,
                                          uint32_t nthreads) {
     const uint32_t K = a.K, lc = a.log_cols;
@@ -175,19 +208,9 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
     const bool active = tid < nthreads;
 
     // ---- load (columns fastest for strided passes, rows fastest for the last)
-    if (!a.pre && !a.pw_b) {
-        // 16-byte units: 8 lanes copy the low halves of 8 elements, the next 8
-        // lanes their high halves (tiles under 8 elements: element-major)
-        const bool grouped = CN >= 8;
-        for (uint32_t u = tid; active && u < 2 * CN; u += nthreads) {
-            const uint32_t e = grouped ? ((u & 7u) | ((u >> 4) << 3)) : (u >> 1);
-            const uint32_t half = grouped ? ((u >> 3) & 1u) : (u & 1u);
-            uint32_t d, cc;
-            if (a.last) { d = e & (N - 1); cc = e >> K; }
-            else        { cc = e & (C - 1); d = e >> lc; }
-            const size_t g = tile_src(a, tile, d, cc);
-            cp_async16((half ? s_hi : s_lo) + smem_slot(cc, d, K, lc), a.in + 2 * g + half);
-        }
+    if (PRELOADED) {
+    } else if (!a.pre && !a.pw_b) {
+        issue_tile_load(a, smem, tile, nthreads);
         cp_async_wait_all();
     } else {
         for (uint32_t e = tid; active && e < CN; e += nthreads) {
@@ -210,13 +233,17 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
             sts_elem(s_lo, s_hi, smem_slot(cc, d, K, lc), x);
         }
     }
-    __syncthreads();
+    if (!PRELOADED) __syncthreads();
 
     // ---- stages 0 .. K-3: radix-2 butterflies through shared memory.  Each
     // thread takes ILP independent butterflies per step (every thread owns at
     // least two per stage: nthreads <= C*N/4), so the carry chains and loads of
     // one overlap with the other's product.
-    for (uint32_t s = 0; s + 2 < K; s++) {
+    // SHFL: the stages with pair distance 16, 8 and 4 run in registers with
+    // warp shuffles (below) instead of through shared memory
+    const bool shfl_tail = SHFL && K >= 6 && nthreads >= 32;
+    const uint32_t s_end = shfl_tail ? K - 5 : K - 2;
+    for (uint32_t s = 0; s < s_end; s++) {
         const uint32_t lh = K - 1 - s;
         const uint32_t h = 1u << lh;
         const uint4 *ws = a.w_stage + 2 * size_t(N - 2 * h);
@@ -292,6 +319,47 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
         }
         }
         __syncthreads();
+    }
+
+    if constexpr (SHFL) {
+        if (shfl_tail) {
+            // A warp holds the 64 rows of one group (2 per lane) for the stages
+            // with pair distance h = 16, 8, 4.  At distance 2^lh lane L holds
+            // the pair (d, d + 2^lh), d = L with a zero inserted at bit lh; for
+            // the next distance, lanes L and L ^ 2^(lh-1) exchange one element
+            // (the one the partner's next pair needs) with 8 shuffles.
+            const uint32_t lane = tid & 31u, warp = tid >> 5, nwarps = nthreads >> 5;
+            const uint32_t groups = CN >> 6;
+            for (uint32_t gi = warp; active && gi < groups; gi += nwarps) {
+                const uint32_t cc = gi >> (K - 6), base = (gi & ((N >> 6) - 1)) << 6;
+                uint32_t d0 = ((lane >> 4) << 5) | (lane & 15u);
+                uint32_t x[8], y[8];
+                lds_elem(x, s_lo, s_hi, smem_slot(cc, base + d0, K, lc));
+                lds_elem(y, s_lo, s_hi, smem_slot(cc, base + d0 + 16, K, lc));
+                for (uint32_t lh = 4; lh >= 2; lh--) {
+                    const uint32_t h = 1u << lh;
+                    uint32_t w[8], t[8];
+                    ldg_elem(w, a.w_stage + 2 * (size_t(N - 2 * h) + (d0 & (h - 1))));
+                    sub_lazy<F>(t, x, y);
+                    add<F>(x, x, y);
+                    mul<F>(y, w, t);
+                    if (lh > 2) {
+                        const uint32_t m = h >> 1;
+                        const bool beta = (lane >> (lh - 1)) & 1u;
+#pragma unroll
+                        for (int k = 0; k < 8; k++) {
+                            const uint32_t r = __shfl_xor_sync(0xffffffffu, beta ? x[k] : y[k], m);
+                            if (beta) x[k] = r;
+                            else y[k] = r;
+                        }
+                        d0 = ((lane >> (lh - 1)) << lh) | (lane & (m - 1));
+                    }
+                }
+                sts_elem(s_lo, s_hi, smem_slot(cc, base + d0, K, lc), x);
+                sts_elem(s_lo, s_hi, smem_slot(cc, base + d0 + 4, K, lc), y);
+            }
+            __syncthreads();
+        }
     }
 
     // ---- last two stages as radix-4 on rows d0..d0+3 (columns fastest)
@@ -379,18 +447,51 @@ __host__ __device__ constexpr uint32_t pass_threads_for(uint32_t K, uint32_t lc,
 //   5: as 3 with twice the threads per tile (one butterfly per thread per
 //      stage; half the threads idle in the radix-4 epilogue): more warps in
 //      flight for transforms too small to fill the GPU
+//   6: as 3 with two tile buffers: the next tile's loads overlap this tile's
+//      stages (twice the shared memory per block)
+//   7: as 1 with the stages of pair distance 16, 8 and 4 in registers, the
+//      partners exchanged by warp shuffles (digits of 6 bits or more)
 template <int V> struct PassVariant;
 template <> struct PassVariant<1> { static constexpr int ILP = 1, MIN_BLOCKS = 3; };
 template <> struct PassVariant<2> { static constexpr int ILP = 2, MIN_BLOCKS = 2; };
 template <> struct PassVariant<3> { static constexpr int ILP = 1, MIN_BLOCKS = 4; };
 template <> struct PassVariant<4> { static constexpr int ILP = 0, MIN_BLOCKS = 2; };  // pipelined
 template <> struct PassVariant<5> { static constexpr int ILP = 1, MIN_BLOCKS = 4; };  // 2x threads
+template <> struct PassVariant<6> { static constexpr int ILP = 1, MIN_BLOCKS = 4; };  // 2 buffers
+template <> struct PassVariant<7> { static constexpr int ILP = 1, MIN_BLOCKS = 3; };  // shuffles
 
 template <class F, int V>
 __global__ void __launch_bounds__(256, PassVariant<V>::MIN_BLOCKS) ntt_pass_kernel(const PassArgs a) {
     extern __shared__ uint4 smem[];
-    for (uint32_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x)
-        run_tile<F, PassVariant<V>::ILP>(a, smem, tile, blockDim.x);
+    if (V != 6 || a.pre || a.pw_b) {
+        for (uint32_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x)
+            run_tile<F, PassVariant<V>::ILP, false, V == 7>(a, smem, tile, blockDim.x);
+        return;
+    }
+    // Variant 6: two tile buffers.  The copies of the block's next tile are in
+    // flight (cp.async group) while the current tile's stages run, so a tile's
+    // load latency overlaps the previous tile's arithmetic within the block.
+    // The buffer a load goes to was last used by the tile before, which ended
+    // with a block barrier.
+    const uint32_t CN = 1u << (a.K + a.log_cols);
+    uint32_t tile = blockIdx.x;
+    if (tile >= a.num_tiles) return;
+    issue_tile_load(a, smem, tile, blockDim.x);
+    cp_async_commit();
+    uint32_t cur = 0;
+    for (; tile < a.num_tiles; tile += gridDim.x) {
+        const uint32_t next = tile + gridDim.x;
+        if (next < a.num_tiles) {
+            issue_tile_load(a, smem + (cur ^ 1u) * 2 * CN, next, blockDim.x);
+            cp_async_commit();
+            cp_async_wait_group<1>();
+        } else {
+            cp_async_wait_group<0>();
+        }
+        __syncthreads();
+        run_tile<F, 1, true>(a, smem + cur * 2 * CN, tile, blockDim.x);
+        cur ^= 1u;
+    }
 }
 
 }  // namespace zkntt

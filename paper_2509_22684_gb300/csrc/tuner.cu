@@ -211,7 +211,10 @@ zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_can
         splits(log_n, p, sp);
         for (auto &d : sp)
             for (int mode : {ZKNTT_TWIDDLE_PRECOMP, ZKNTT_TWIDDLE_OTF})
-                for (int ilp = 1; ilp <= NUM_VARIANTS; ilp++)
+                // variants 6 (two tile buffers) and 7 (warp-shuffle stages) were
+                // measured slower than 3 and 1 at every size and stay explicit
+                // options only
+                for (int ilp = 1; ilp <= TUNED_VARIANTS; ilp++)
                 for (int cap = 3; cap >= 1; cap--) {
                     if (p == 1 && (mode == ZKNTT_TWIDDLE_OTF || cap != 3)) continue;
                     Cand c;

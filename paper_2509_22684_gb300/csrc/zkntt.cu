@@ -254,7 +254,8 @@ zkntt_status device_info(DeviceInfo **out) {
         for (int f = 0; f < NUM_FIELDS; f++)
             for (int ilp = 1; ilp <= NUM_VARIANTS; ilp++)
                 ZK_CHECK(cudaFuncSetAttribute(field_kernels(f).pass[ilp],
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (ilp == 6 ? 128 : 64) * 1024));
         for (int f = 0; f < NUM_FIELDS; f++) {
             ZK_CHECK(cudaFuncSetAttribute(batch_kernel_ptr(f),
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
@@ -543,6 +544,7 @@ zkntt_status build_plan(zkntt_plan_s *P, const zkntt_plan_options *opts) {
                             : (uint32_t(1) << (ps.hi_bits + ps.lo_bits - lc));
         ps.threads = int(pass_threads_for(uint32_t(ps.K), uint32_t(lc), ilp));
         ps.smem = size_t(32) << (ps.K + lc);
+        if (ilp == 6) ps.smem *= 2;  // two tile buffers
         int nb = 0;
         ZK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &nb, field_kernels(P->field).pass[ps.ilp], ps.threads, ps.smem));

@@ -220,7 +220,7 @@ def test_argument_errors():
 
 @pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
 @pytest.mark.parametrize("kind", KINDS)
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("digits,cols", [((8, 8), None), ((5, 6, 5), None), ((11, 5), (1, 8)),
                                          ((4, 4, 4, 4), (8, 8, 8, 8)), ((10,), None), ((3,), None),
                                          ((7, 9), (4, 2))])

@@ -41,4 +41,4 @@ def test_every_entry_is_a_valid_schedule():
         assert 1 <= p <= 4 and sum(digits) == r["log_n"], r
         assert all(1 <= k <= 11 for k in digits), r
         assert all(0 <= c <= 3 and k + c <= 11 for k, c in zip(digits, cols)), r
-        assert r["mode"] in (1, 2) and 1 <= r["ilp"] <= 5 and r["ms"] > 0, r
+        assert r["mode"] in (1, 2) and 1 <= r["ilp"] <= 7 and r["ms"] > 0, r
