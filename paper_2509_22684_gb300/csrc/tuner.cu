@@ -151,7 +151,7 @@ void splits(int L, int p, std::vector<std::vector<int>> &out) {
 
 using namespace zkntt;
 
-extern "C" // The tuning input: uniform field elements (SplitMix64 words, rejection-sampled
+// The tuning input: uniform field elements (SplitMix64 words, rejection-sampled
 // below r) rather than zeros, so the candidates are timed on the bit activity --
 // and hence the power draw and sustained clock -- of real data.  A block of
 // 2^16 elements is drawn on the host and repeated over the vector by
@@ -197,55 +197,39 @@ static zkntt_status fill_uniform(zkntt_field field, void *d, size_t n) {
     return ZKNTT_OK;
 }
 
-zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_candidates,
+// Candidate schedules for one digit split: both twiddle modes, variants
+// 1 .. TUNED_VARIANTS (6 and 7 were measured slower than 3 and 1 at every size
+// and stay explicit options), column caps 3..1.
+static void split_candidates(int log_n, const std::vector<int> &d, std::vector<zkntt_plan_options> &out) {
+    const int p = int(d.size());
+    for (int mode : {ZKNTT_TWIDDLE_PRECOMP, ZKNTT_TWIDDLE_OTF})
+        for (int ilp = 1; ilp <= TUNED_VARIANTS; ilp++)
+            for (int cap = 3; cap >= 1; cap--) {
+                if (p == 1 && (mode == ZKNTT_TWIDDLE_OTF || cap != 3)) continue;
+                zkntt_plan_options o;
+                memset(&o, 0, sizeof o);
+                o.twiddle_mode = mode;
+                o.ilp = ilp;
+                o.num_passes = p;
+                int hi = 0;
+                for (int i = 0; i < p; i++) {
+                    o.digit_bits[i] = d[i];
+                    int span = (i == p - 1) ? hi : (log_n - hi - d[i]);
+                    int lc = std::min({cap, MAX_DIGIT_BITS - d[i], span});
+                    o.cols_per_cta[i] = 1 << std::max(0, lc);
+                    hi += d[i];
+                }
+                out.push_back(o);
+            }
+}
+
+extern "C" zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_candidates,
                                    zkntt_tune_result *best) {
     if (field < 0 || field >= NUM_FIELDS) return ZKNTT_EINVAL;
     if (log_n < 1 || log_n > 28 || max_candidates < 1) return ZKNTT_EINVAL;
-    struct Cand {
-        zkntt_plan_options o;
-    };
-    std::vector<Cand> cands;
+    std::vector<std::vector<int>> all_splits;
     int pmin = (log_n + MAX_DIGIT_BITS - 1) / MAX_DIGIT_BITS;
-    for (int p = pmin; p <= std::min(4, pmin + 1); p++) {
-        std::vector<std::vector<int>> sp;
-        splits(log_n, p, sp);
-        for (auto &d : sp)
-            for (int mode : {ZKNTT_TWIDDLE_PRECOMP, ZKNTT_TWIDDLE_OTF})
-                // variants 6 (two tile buffers) and 7 (warp-shuffle stages) were
-                // measured slower than 3 and 1 at every size and stay explicit
-                // options only
-                for (int ilp = 1; ilp <= TUNED_VARIANTS; ilp++)
-                for (int cap = 3; cap >= 1; cap--) {
-                    if (p == 1 && (mode == ZKNTT_TWIDDLE_OTF || cap != 3)) continue;
-                    Cand c;
-                    memset(&c.o, 0, sizeof c.o);
-                    c.o.twiddle_mode = mode;
-                    c.o.ilp = ilp;
-                    c.o.num_passes = p;
-                    int hi = 0;
-                    for (int i = 0; i < p; i++) {
-                        c.o.digit_bits[i] = d[i];
-                        int span = (i == p - 1) ? hi : (log_n - hi - d[i]);
-                        int lc = std::min({cap, MAX_DIGIT_BITS - d[i], span});
-                        c.o.cols_per_cta[i] = 1 << std::max(0, lc);
-                        hi += d[i];
-                    }
-                    cands.push_back(c);
-                }
-    }
-    // prefer balanced splits and precomputed tables first when the budget is small
-    std::stable_sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) {
-        auto spread = [](const zkntt_plan_options &o) {
-            int mx = 0, mn = 99;
-            for (int i = 0; i < o.num_passes; i++) {
-                mx = std::max(mx, o.digit_bits[i]);
-                mn = std::min(mn, o.digit_bits[i]);
-            }
-            return (mx - mn) * 4 + (o.twiddle_mode == ZKNTT_TWIDDLE_OTF ? 2 : 0);
-        };
-        return spread(a.o) < spread(b.o);
-    });
-    if (int(cands.size()) > max_candidates) cands.resize(max_candidates);
+    for (int p = pmin; p <= std::min(4, pmin + 1); p++) splits(log_n, p, all_splits);
 
     const size_t bytes = size_t(32) << log_n;
     void *in = nullptr, *out = nullptr, *scr = nullptr;
@@ -258,11 +242,11 @@ zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_can
         result = ZKNTT_ENOMEM;
     }
     if (result == ZKNTT_OK) result = fill_uniform(field, in, size_t(1) << log_n);
-    TuneEntry bestE;
-    double best_ms = 1e30;
-    for (size_t ci = 0; ci < cands.size() && result == ZKNTT_OK; ci++) {
+
+    // median time of one schedule over `samples` samples; < 0 if it cannot run
+    auto time_one = [&](const zkntt_plan_options &o, int samples) -> double {
         zkntt_plan plan = nullptr;
-        if (zkntt_plan_create_ex(&plan, field, log_n, dir, nullptr, &cands[ci].o) != ZKNTT_OK) continue;
+        if (zkntt_plan_create_ex(&plan, field, log_n, dir, nullptr, &o) != ZKNTT_OK) return -1;
         bool ok = true;
         for (int w = 0; w < 2 && ok; w++)
             ok = zkntt_execute_scratch(plan, in, out, scr, bytes, s) == ZKNTT_OK;
@@ -280,7 +264,7 @@ zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_can
             reps = std::max(1, std::min(200, int(1.0f / std::max(one, 1e-3f)) + 1));
         }
         std::vector<float> t;
-        for (int r = 0; r < 5 && ok; r++) {
+        for (int r = 0; r < samples && ok; r++) {
             cudaEventRecord(e0, s);
             for (int k = 0; k < reps && ok; k++)
                 ok = zkntt_execute_scratch(plan, in, out, scr, bytes, s) == ZKNTT_OK;
@@ -291,23 +275,59 @@ zkntt_status zkntt_tune(zkntt_field field, int log_n, zkntt_dir dir, int max_can
             t.push_back(ms / float(reps));
         }
         zkntt_plan_destroy(plan);
-        if (!ok || t.empty()) continue;
+        if (!ok || t.empty()) return -1;
         std::sort(t.begin(), t.end());
-        double med = t[t.size() / 2];
+        return t[t.size() / 2];
+    };
+
+    // Stage 1: every digit split with one representative schedule (precomputed
+    // tables; for small sizes the variant with twice the threads and wider
+    // tiles, else the 64-register variant with 2-column tiles).
+    std::vector<std::pair<double, size_t>> ranked;
+    for (size_t si = 0; si < all_splits.size() && result == ZKNTT_OK; si++) {
+        std::vector<zkntt_plan_options> c;
+        split_candidates(log_n, all_splits[si], c);
+        const int want_ilp = log_n <= 16 ? 5 : 3, want_cap = log_n <= 16 ? 2 : 1;
+        zkntt_plan_options rep = c.front();
+        for (const auto &o : c) {
+            int cap = 0;
+            for (int i = 0; i < o.num_passes; i++) cap = std::max(cap, o.cols_per_cta[i]);
+            if (o.twiddle_mode == ZKNTT_TWIDDLE_PRECOMP && o.ilp == want_ilp &&
+                cap <= (1 << want_cap)) {
+                rep = o;
+                break;
+            }
+        }
+        const double ms = all_splits.size() > 1 ? time_one(rep, 3) : 0.0;
+        if (ms >= 0) ranked.push_back({ms, si});
+    }
+    std::stable_sort(ranked.begin(), ranked.end());
+    // Stage 2: every schedule of the best three splits, best split first,
+    // within the candidate budget.
+    std::vector<zkntt_plan_options> cands;
+    for (size_t k = 0; k < ranked.size() && k < 3; k++)
+        split_candidates(log_n, all_splits[ranked[k].second], cands);
+    if (int(cands.size()) > max_candidates) cands.resize(max_candidates);
+
+    TuneEntry bestE;
+    double best_ms = 1e30;
+    for (size_t ci = 0; ci < cands.size() && result == ZKNTT_OK; ci++) {
+        const double med = time_one(cands[ci], 5);
+        if (med < 0) continue;
         if (med < best_ms) {
             best_ms = med;
-            bestE.passes = cands[ci].o.num_passes;
+            bestE.passes = cands[ci].num_passes;
             for (int i = 0; i < 4; i++) {
-                bestE.digits[i] = cands[ci].o.digit_bits[i];
-                int c = cands[ci].o.cols_per_cta[i], l = 0;
+                bestE.digits[i] = cands[ci].digit_bits[i];
+                int c = cands[ci].cols_per_cta[i], l = 0;
                 while (c > 1) {
                     c >>= 1;
                     l++;
                 }
                 bestE.log_cols[i] = i < bestE.passes ? l : -1;
             }
-            bestE.mode = cands[ci].o.twiddle_mode;
-            bestE.ilp = cands[ci].o.ilp;
+            bestE.mode = cands[ci].twiddle_mode;
+            bestE.ilp = cands[ci].ilp;
             bestE.ms = med;
         }
     }
