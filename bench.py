@@ -482,6 +482,58 @@ def groth16_only(args) -> None:
     print(json.dumps(out), flush=True)
 
 
+def calibrate(args) -> None:
+    """The multiply forms and the Montgomery product on their own (one JSON
+    line): zkntt_imadbench's five modes and zkntt_mulbench for the field."""
+    import torch
+
+    import paper_2509_22684_gb300 as zk
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    out = {"forms_per_s_T": {k: round(v / 1e12, 3)
+                              for k, v in measured_imad_peak(zk, torch, sms, stream).items()
+                              if k.endswith("_per_s")}}
+    blocks, threads, iters = sms * 8, 256, 256
+    sink = torch.empty(blocks * threads, dtype=torch.int32, device="cuda")
+    zk.mulbench(args.field, blocks, threads, 8, sink, stream=stream)
+    best = min(timed(lambda: zk.mulbench(args.field, blocks, threads, iters, sink, stream=stream),
+                     stream, 1) for _ in range(3))
+    out["mulbench_products_per_s_G"] = round(blocks * threads * 4 * iters / (best / 1e3) / 1e9, 2)
+    out["field"] = args.field
+    out["library"] = os.environ.get("ZKNTT_LIB", "paper_2509_22684_gb300/libzkntt.so")
+    print(json.dumps(out), flush=True)
+
+
+def sharded_emulated(args) -> None:
+    """One transform of 2^L split over G shards (paper_2509_22684_gb300.sharded),
+    all shards run in this process on this GPU with the exchange done by
+    copies, against the plain transform of the same size (one JSON line).  It
+    measures the sharded algorithm's own device work on one GPU, not a
+    multi-GPU run."""
+    import numpy as np
+    import torch
+
+    import paper_2509_22684_gb300 as zk
+    from paper_2509_22684_gb300.sharded import LibraryOps, ShardedNTT, emulate, scatter_input
+    from workloads import uniform_elements
+    field, L, G = args.field, args.log_n, args.sharded
+    stream = torch.cuda.current_stream()
+    x = torch.from_numpy(uniform_elements(FIELD_R[field], 1 << L, 2024).view(np.int32)).cuda()
+    ops = LibraryOps(field)
+    shards = [ShardedNTT(field, L, G, r, ops=ops) for r in range(G)]
+    xs = scatter_input(x, G)
+    plan = zk.Plan(field, L)
+    out = {"workload": f"{field} forward NTT n=2^{L}", "shards": G, "steps": args.steps}
+    for name, f in (("plain_ms", lambda: plan.execute(x)), ("sharded_emulated_ms", lambda: emulate(shards, xs))):
+        for _ in range(args.warmup):
+            f()
+        out[name] = round(timed(f, stream, args.steps) / args.steps, 4)
+    out["ratio"] = round(out["sharded_emulated_ms"] / out["plain_ms"], 3)
+    plan.close()
+    ops.close()
+    print(json.dumps(out), flush=True)
+
+
 def sweep(args) -> None:
     """One JSON line per (field, kind, log_n, twiddle mode): the full grid of
     single-transform configurations, device-resident inputs, CUDA-event
@@ -558,7 +610,13 @@ def run_ours(args, world, rank, local):
     X = uniform_elements(FIELD_R[field], n, 2024 + rank)
     x = torch.from_numpy(X.view(np.int32)).cuda()
     y = torch.empty_like(x)
-    plan = zk.Plan(field, L)
+    if args.variant:
+        # force a pass-kernel variant on the shipped digit split and columns
+        sched = json.loads(tuned_schedule(FIELD_IDS[field], L))
+        plan = zk.Plan(field, L, digits=sched["digits"], cols=[1 << c for c in sched["log_cols"]],
+                       ilp=args.variant, twiddle_mode={1: "precomp", 2: "otf"}[sched["mode"]])
+    else:
+        plan = zk.Plan(field, L)
     desc = plan.describe()
     scratch = torch.empty(plan.scratch_bytes() // 4, dtype=torch.int32, device="cuda")
     step = lambda: plan.execute_scratch(x, y, scratch, stream=stream)
@@ -619,7 +677,8 @@ def run_ours(args, world, rank, local):
     value = world * n * args.steps / (ms_max / 1e3) / 1e6
     workload = f"{field} forward NTT n=2^{L}"
     khash = kernel_source_hash()
-    traffic = recorded_traffic(khash, workload, tuned_schedule(FIELD_IDS[field], L))
+    traffic = None if args.variant else recorded_traffic(khash, workload,
+                                                         tuned_schedule(FIELD_IDS[field], L))
     result = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -634,6 +693,7 @@ def run_ours(args, world, rank, local):
         "dtype": "u32 (8x32-bit limb Montgomery F_r, exact)",
         "data": "synthetic (SplitMix64 uniform field elements, seed 2024+rank)",
         "config": {"workload": workload, "field": field, "log_n": L, "direction": "forward",
+                   "variant": args.variant or "shipped schedule",
                    "passes": passes, "digits": desc["digits"], "twiddle_mode": desc["twiddle_mode"],
                    "l2": "inputs larger than L2 (512 MiB per vector vs 129 MB)",
                    "parallelism": f"replicas x{world}"},
@@ -747,6 +807,12 @@ def main():
                     help="print one line per field x kind x size x twiddle mode instead")
     ap.add_argument("--sweep-sizes", default="16,20,22,24,26")
     ap.add_argument("--sweep-fields", default="bls12_381_fr,bn254_fr,bls12_377_fr")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="force pass-kernel variant V on the shipped digit split (study runs)")
+    ap.add_argument("--calibrate", action="store_true",
+                    help="print the multiply-form and product rates instead")
+    ap.add_argument("--sharded", type=int, default=0, metavar="G",
+                    help="time the sharded transform's G shards emulated on this GPU instead")
     ap.add_argument("--groth16", type=int, default=0, metavar="L",
                     help="time only the Groth16 H sequence at 2^L (fused graph vs separate)")
     args = ap.parse_args()
@@ -762,6 +828,12 @@ def main():
         return
     if args.groth16:
         groth16_only(args)
+        return
+    if args.calibrate:
+        calibrate(args)
+        return
+    if args.sharded:
+        sharded_emulated(args)
         return
     world, rank, local = dist_init(args)
     try:

@@ -242,7 +242,8 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
     // SHFL: the stages with pair distance 16, 8 and 4 run in registers with
     // warp shuffles (below) instead of through shared memory
     const bool shfl_tail = SHFL && K >= 6 && nthreads >= 32;
-    const uint32_t s_end = shfl_tail ? K - 5 : K - 2;
+    // (K < 3: no loop stages; K - 2 must not wrap around)
+    const uint32_t s_end = shfl_tail ? K - 5 : (K > 2 ? K - 2 : 0u);
     for (uint32_t s = 0; s < s_end; s++) {
         const uint32_t lh = K - 1 - s;
         const uint32_t h = 1u << lh;
