@@ -239,14 +239,21 @@ zkntt_status zkntt_flags_destroy(uint32_t *host_view);
  *   H_i = (A_i B_i - C_i) * (g^n - 1)^-1     (Z(x) = x^n - 1 on the coset g*w^i)
  *   d_h = cosetINTT_g(H)
  * with g the field's multiplicative generator.  d_a, d_b, d_c, d_h: n elements
- * each (inputs are read only).  d_scratch: 3 * n * 32 bytes of caller-owned
- * device memory.  fused = 1 runs the whole sequence as one persistent launch
- * (pointwise fused into the last transform's first pass); fused = 0 issues the
- * seven transforms and the pointwise kernel as separate launches.
+ * each (inputs are read only; d_h must not overlap them).  d_scratch: 3 * n * 32
+ * bytes of caller-owned device memory.  Runs the whole sequence as one
+ * persistent launch (pointwise fused into the last transform's first pass);
+ * further scratch comes from the library's stream-ordered pool.  log_n 1..28.
  */
 zkntt_status zkntt_groth16_h(zkntt_field field, int log_n, const void *d_a, const void *d_b,
-                             const void *d_c, void *d_h, void *d_scratch, int fused,
-                             void *stream);
+                             const void *d_c, void *d_h, void *d_scratch, void *stream);
+
+/* As zkntt_groth16_h (Fig. 2), choosing the form: fused = 1 is the single
+ * persistent launch; fused = 0 issues the seven transforms and the pointwise
+ * kernel as separate launches (the form the paper finds in provers, Section
+ * IV-A), for comparison. */
+zkntt_status zkntt_groth16_h_ex(zkntt_field field, int log_n, const void *d_a, const void *d_b,
+                                const void *d_c, void *d_h, void *d_scratch, int fused,
+                                void *stream);
 
 /*
  * The fused Groth16 H sequence (Fig. 2) captured once into a CUDA graph (the

@@ -260,9 +260,9 @@ def groth16_h(field, log_n: int, a, b, c, h=None, scratch=None, fused: bool = Tr
     for t in (a, b, c, h):
         if t.numel() != 8 * n:
             raise ValueError("vector size mismatch")
-    N.check(N.lib().zkntt_groth16_h(_field_id(field), log_n, _ptr(a), _ptr(b), _ptr(c), _ptr(h),
-                                    _ptr(scratch), int(fused), _stream_handle(stream)),
-            "zkntt_groth16_h")
+    N.check(N.lib().zkntt_groth16_h_ex(_field_id(field), log_n, _ptr(a), _ptr(b), _ptr(c),
+                                       _ptr(h), _ptr(scratch), int(fused), _stream_handle(stream)),
+            "zkntt_groth16_h_ex")
     return h
 
 

@@ -63,7 +63,8 @@ SIGNATURES = {
     "zkntt_execute_batch_signal": [ctypes.POINTER(_vp), ctypes.POINTER(IO), _i, _vp, ctypes.c_uint32, _vp],
     "zkntt_flags_create": [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "zkntt_flags_destroy": [_vp],
-    "zkntt_groth16_h": [_i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp],
+    "zkntt_groth16_h": [_i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
+    "zkntt_groth16_h_ex": [_i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp],
     "zkntt_groth16_graph_create": [ctypes.POINTER(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
     "zkntt_graph_launch": [_vp, _vp],
     "zkntt_graph_destroy": [_vp],

@@ -1248,7 +1248,12 @@ zkntt_status zkntt_flags_destroy(uint32_t *host_view) {
 }
 
 zkntt_status zkntt_groth16_h(zkntt_field field, int log_n, const void *d_a, const void *d_b,
-                             const void *d_c, void *d_h, void *d_scratch, int fused, void *stream) {
+                             const void *d_c, void *d_h, void *d_scratch, void *stream) {
+    return zkntt_groth16_h_ex(field, log_n, d_a, d_b, d_c, d_h, d_scratch, 1, stream);
+}
+
+zkntt_status zkntt_groth16_h_ex(zkntt_field field, int log_n, const void *d_a, const void *d_b,
+                                const void *d_c, void *d_h, void *d_scratch, int fused, void *stream) {
     if (!valid_field(field)) return ZKNTT_EINVAL;
     if (log_n < 1 || log_n > 28) return ZKNTT_EINVAL;
     if (bad_ptr(d_a) || bad_ptr(d_b) || bad_ptr(d_c) || bad_ptr(d_h) || bad_ptr(d_scratch))
@@ -1349,7 +1354,7 @@ zkntt_status zkntt_groth16_graph_create(zkntt_graph *out, zkntt_field field, int
         delete g;
         return from_cuda(e);
     }
-    st = zkntt_groth16_h(field, log_n, d_a, d_b, d_c, d_h, d_scratch, 1, stream);
+    st = zkntt_groth16_h_ex(field, log_n, d_a, d_b, d_c, d_h, d_scratch, 1, stream);
     e = cudaStreamEndCapture(s, &g->graph);
     if (st == ZKNTT_OK && e == cudaSuccess)
         e = cudaGraphInstantiate(&g->exec, g->graph, 0);

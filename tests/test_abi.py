@@ -66,7 +66,8 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.zkntt_execute_batch(None, None, -1, None) == N.EINVAL
     assert lib.zkntt_execute_batch(None, None, 0, None) == N.OK          # empty batch: no-op
     assert lib.zkntt_execute_batch(None, None, 0, None) == N.OK
-    assert lib.zkntt_groth16_h(0, 10, None, None, None, None, None, 1, None) == N.EINVAL
+    assert lib.zkntt_groth16_h(0, 10, None, None, None, None, None, None) == N.EINVAL
+    assert lib.zkntt_groth16_h_ex(0, 10, None, None, None, None, None, 1, None) == N.EINVAL
     assert lib.zkntt_plan_destroy(None) == N.OK
     err = ctypes.c_int(-1)
     assert lib.zkntt_last_cuda_error(ctypes.byref(err)) == N.OK

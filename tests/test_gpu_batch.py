@@ -238,3 +238,21 @@ def test_batch_larger_than_one_segment_table_is_split():
     flags.close()
     for p in plans:
         p.close()
+
+
+def test_groth16_contract_signature_runs_the_fused_form():
+    """zkntt_groth16_h with the boundary's own signature (no form argument)
+    runs the fused sequence and equals the oracle (Fig. 2)."""
+    import torch
+    from paper_2509_22684_gb300 import _native as N
+    F = fld.BN254
+    L = 10
+    A, B, C = (uniform_elements(F.r, 1 << L, s) for s in (3101, 3102, 3103))
+    a, b, c = to_dev(A), to_dev(B), to_dev(C)
+    h = torch.empty_like(a)
+    scr = torch.empty((3 << L, 8), dtype=torch.int32, device="cuda")
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    st = N.lib().zkntt_groth16_h(1, L, p(a), p(b), p(c), p(h), p(scr),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == N.OK
+    assert np.array_equal(to_host(h), ref.groth16_h_mont(F, A, B, C))
