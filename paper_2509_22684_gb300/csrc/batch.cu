@@ -74,7 +74,9 @@ __global__ void __launch_bounds__(BATCH_THREADS, BATCH_MIN_BLOCKS)
         // one butterfly per thread per stage (as pass variant 5): small tiles
         // keep twice the threads of the block busy
         const uint32_t nt = pass_threads_for(sg.a.K, sg.a.log_cols, 5);
-        run_tile<F, 1>(sg.a, smem, tile, nt < BATCH_THREADS ? nt : BATCH_THREADS);
+        // (without the shared-twiddle pairing: at this kernel's 64-register
+        // budget it adds spills)
+        run_tile<F, 1, false, false, false>(sg.a, smem, tile, nt < BATCH_THREADS ? nt : BATCH_THREADS);
         // run_tile ends with a block barrier: every store of the tile is issued
         if (threadIdx.x == 0) {
             __threadfence();

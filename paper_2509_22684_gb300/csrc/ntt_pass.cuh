@@ -194,8 +194,9 @@ __device__ __forceinline__ void issue_tile_load(const PassArgs &a, uint4 *smem, 
 
 // Process one tile with `nthreads` threads of the block (threads at or beyond
 // nthreads only take part in the barriers).  PRELOADED: the caller has
-// already copied the tile into `smem` and synchronised the block.
-template <class F, int ILP, bool PRELOADED = false, bool SHFL = false>
+// already copied the tile into `smem` and synchronised the block.  PAIR: let a
+// thread's two butterflies of one row pair share their twiddle (below).
+template <class F, int ILP, bool PRELOADED = false, bool SHFL = false, bool PAIR = true>
 __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_t tile,
                                          uint32_t nthreads) {
     const uint32_t K = a.K, lc = a.log_cols;
@@ -287,6 +288,33 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
                 }
                 s0 = n0;
                 s1 = n1;
+            }
+        } else if (PAIR && ILP == 1 && lc >= 1 && (CN >> 1) == 2 * nthreads) {
+            // Each thread owns two butterflies, bk = tid and tid + C N/4: the
+            // same row pair in columns cc and cc + C/2, so one twiddle serves
+            // both and the second pair's slot is the first's moved by C/2
+            // columns, its swizzle term flipped in bit 2.
+            if (active) {
+                const uint32_t cc = tid >> (K - 1);
+                const uint32_t b = tid & ((N >> 1) - 1);
+                const uint32_t j = b & (h - 1);
+                const uint32_t i0 = ((b >> lh) << (lh + 1)) | j;
+                const uint32_t q0 = smem_slot(cc, i0, K, lc);
+                const uint32_t q0b = (q0 + ((C >> 1) << K)) ^ (K >= 3 ? 4u : 0u);
+                uint32_t w[8];
+                ldg_elem(w, ws + 2 * size_t(j));
+#pragma unroll 1
+                for (int q = 0; q < 2; q++) {
+                    const uint32_t a0 = q ? q0b : q0;
+                    uint32_t x[8], y[8], t[8];
+                    lds_elem(x, s_lo, s_hi, a0);
+                    lds_elem(y, s_lo, s_hi, a0 ^ step);
+                    sub_lazy<F>(t, x, y);
+                    add<F>(x, x, y);
+                    mul<F>(y, w, t);
+                    sts_elem(s_lo, s_hi, a0, x);
+                    sts_elem(s_lo, s_hi, a0 ^ step, y);
+                }
             }
         } else {
         for (uint32_t bg = tid; active && bg < (CN >> 1); bg += ILP * nthreads) {
