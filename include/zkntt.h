@@ -356,6 +356,19 @@ zkntt_status zkntt_field_op(zkntt_field field, int op, const void *d_a, const vo
 zkntt_status zkntt_scale_powers(zkntt_field field, const void *d_x, void *d_out, size_t n,
                                 const uint32_t *c_mont, const uint32_t *base_mont, void *stream);
 
+/* G-point transforms over whole blocks (G = 2^log_g, log_g 1..3): with the
+ * input laid out as G blocks of b elements (element r * b + i), for every
+ * column i < b
+ *     d_out[k * b + i] = sum_r d_in[r * b + i] * w^(r k)      (r, k < G)
+ * where w is the field's root of order G (its inverse when inverse != 0; no
+ * 1/G factor).  This is the last step of the four-step decomposition
+ * (Section II-B) when the sub-transforms of the other digit live on
+ * different GPUs: the sharded transform applies it to the blocks it receives
+ * from the G ranks.  In place allowed; partial overlap, bad pointers or
+ * log_g outside 1..3 -> ZKNTT_EINVAL.  Allocates nothing. */
+zkntt_status zkntt_block_dft(zkntt_field field, int log_g, size_t b, const void *d_in, void *d_out,
+                             int inverse, void *stream);
+
 /* Groth16 pointwise step on its own (the (A B - C) / Z step of Fig. 2):
  * d_h_i = (a_i b_i - c_i) * z, z given as 8 Montgomery limbs in host memory. */
 zkntt_status zkntt_pointwise(zkntt_field field, const void *d_a, const void *d_b, const void *d_c,

@@ -17,7 +17,7 @@ from ._native import ZkNttError, FIELDS, TWIDDLE_MODES
 
 __all__ = ["Plan", "ZkNttError", "FIELDS", "execute_batch", "execute_batch_signal",
            "CompletionFlags", "groth16_h", "Groth16Graph", "field_info",
-           "field_op", "pointwise", "scale_powers", "tune", "sync_status", "mulbench", "imadbench", "pool_info",
+           "field_op", "pointwise", "scale_powers", "block_dft", "tune", "sync_status", "mulbench", "imadbench", "pool_info",
            "new_vector"]
 
 
@@ -313,6 +313,18 @@ def scale_powers(field, x, c_mont: int, base_mont: int, out=None, stream=None) -
     N.check(N.lib().zkntt_scale_powers(_field_id(field), _ptr(x), _ptr(out), x.numel() // 8,
                                        N.limbs_of(c_mont), N.limbs_of(base_mont),
                                        _stream_handle(stream)), "zkntt_scale_powers")
+    return out
+
+
+def block_dft(field, x, log_g: int, inverse: bool = False, out=None, stream=None) -> torch.Tensor:
+    """G-point transforms (G = 2^log_g) over the G blocks of x: out[k*b + i] =
+    sum_r x[r*b + i] w^(r k), w the root of order G (inverse: w^-1, no 1/G)."""
+    out = torch.empty_like(x) if out is None else out
+    n = x.numel() // 8
+    if n % (1 << log_g):
+        raise ValueError("the vector must hold G whole blocks")
+    N.check(N.lib().zkntt_block_dft(_field_id(field), int(log_g), n >> log_g, _ptr(x), _ptr(out),
+                                    int(inverse), _stream_handle(stream)), "zkntt_block_dft")
     return out
 
 

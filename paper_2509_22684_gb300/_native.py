@@ -82,6 +82,7 @@ SIGNATURES = {
     "zkntt_selftest_device_check": [ctypes.POINTER(_i), ctypes.POINTER(_i)],
     "zkntt_pool_info": [ctypes.POINTER(_sz), ctypes.POINTER(_sz)],
     "zkntt_scale_powers": [_i, _vp, _vp, _sz, _u32p, _u32p, _vp],
+    "zkntt_block_dft": [_i, _i, _sz, _vp, _vp, _i, _vp],
 }
 
 

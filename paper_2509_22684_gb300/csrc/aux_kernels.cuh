@@ -70,6 +70,58 @@ __global__ void scale_powers_kernel(const uint4 *x, uint4 *out, size_t n, const 
     }
 }
 
+// Powers w^k (k < 4) of the root used by the G-point transforms below
+// (Montgomery form), passed by value.
+struct BlockTw {
+    uint32_t w[4][8];
+};
+
+// G-point transforms over whole blocks: for every column i < b,
+//   out[k * b + i] = sum_r in[r * b + i] w^(r k)      (r, k < G; w of order G)
+// by radix-2 decimation in frequency in registers (G/2 log2 G butterflies, the
+// j = 0 ones without a product), then the bit-reversed positions written back
+// in natural order.  One thread per column; each thread reads its whole
+// column before writing, so in == out is allowed.
+template <class F, int G>
+__global__ void __launch_bounds__(128) block_dft_kernel(const uint4 *in, uint4 *out, size_t b,
+                                                        const BlockTw tw) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < b;
+         i += size_t(gridDim.x) * blockDim.x) {
+        uint32_t v[G][8];
+#pragma unroll
+        for (int r = 0; r < G; r++) ldg_elem(v[r], in + 2 * (size_t(r) * b + i));
+#pragma unroll
+        for (int h = G / 2; h >= 1; h >>= 1) {
+#pragma unroll
+            for (int g0 = 0; g0 < G; g0 += 2 * h) {
+#pragma unroll
+                for (int j = 0; j < h; j++) {
+                    uint32_t t[8];
+                    if (j == 0) {
+                        sub<F>(t, v[g0], v[g0 + h]);
+                    } else {
+                        sub_lazy<F>(t, v[g0 + j], v[g0 + j + h]);
+                    }
+                    add<F>(v[g0 + j], v[g0 + j], v[g0 + j + h]);
+                    if (j == 0) {
+#pragma unroll
+                        for (int l = 0; l < 8; l++) v[g0 + h][l] = t[l];
+                    } else {
+                        mul<F>(v[g0 + j + h], tw.w[j * (G / (2 * h))], t);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < G; p++) {
+            int q = 0;
+#pragma unroll
+            for (int bit = 1; bit < G; bit <<= 1) q = (q << 1) | ((p & bit) ? 1 : 0);
+            st_elem(out + 2 * (size_t(q) * b + i), v[p]);
+        }
+    }
+}
+
 // c = op(a, b) elementwise: 0 mul, 1 add, 2 sub
 template <class F>
 __global__ void field_op_kernel(int op, const uint4 *a, const uint4 *b, uint4 *c, size_t n) {

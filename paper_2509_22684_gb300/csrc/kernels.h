@@ -16,6 +16,7 @@ struct FieldKernels {
     const void *pointwise;
     const void *mulbench;
     const void *scale_powers;
+    const void *block_dft[4];  // block_dft_kernel<F, 2^g> at index g = 1..3
 };
 
 const FieldKernels &kernels_bls12_381();

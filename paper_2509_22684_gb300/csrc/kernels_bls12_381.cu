@@ -18,6 +18,8 @@ const FieldKernels &kernels_bls12_381() {
         (const void *)&pointwise_kernel<F>,
         (const void *)&mulbench_kernel<F>,
         (const void *)&scale_powers_kernel<F>,
+        {nullptr, (const void *)&block_dft_kernel<F, 2>, (const void *)&block_dft_kernel<F, 4>,
+         (const void *)&block_dft_kernel<F, 8>},
     };
     return k;
 }

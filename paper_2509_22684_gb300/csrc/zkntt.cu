@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "../../include/zkntt.h"
+#include "aux_kernels.cuh"
 #include "batch.cuh"
 #include "field.cuh"
 #include "kernels.h"
@@ -1553,6 +1554,34 @@ zkntt_status zkntt_scale_powers(zkntt_field field, const void *d_x, void *d_out,
     }
     zkntt_status st2 = from_cuda(cudaFreeAsync(d_tab, s));
     return st != ZKNTT_OK ? st : st2;
+}
+
+zkntt_status zkntt_block_dft(zkntt_field field, int log_g, size_t b, const void *d_in, void *d_out,
+                             int inverse, void *stream) {
+    if (!valid_field(field) || log_g < 1 || log_g > 3) return ZKNTT_EINVAL;
+    if (b == 0) return ZKNTT_OK;
+    if (bad_ptr(d_in) || bad_ptr(d_out)) return ZKNTT_EINVAL;
+    const size_t G = size_t(1) << log_g;
+    if (partial_overlap(d_in, d_out, G * b * 32)) return ZKNTT_EINVAL;
+    const HostField &F = host_field(field);
+    if (!F.ok) return ZKNTT_ECUDA;
+    DeviceInfo *dev;
+    zkntt_status st = device_info(&dev);
+    if (st != ZKNTT_OK) return st;
+    // w of order G (w_max^(2^(s - g)), or its inverse) and its first powers
+    E8 w = hpow(F, F.wmax, uint64_t(1) << (F.s - log_g));
+    if (inverse) w = hinv(F, w);
+    BlockTw tw;
+    memset(&tw, 0, sizeof tw);
+    E8 cur = F.one;
+    for (size_t k = 0; k < G / 2; k++) {
+        memcpy(tw.w[k], cur.data(), 32);
+        cur = hmul(F, cur, w);
+    }
+    void *args[] = {&d_in, &d_out, &b, &tw};
+    return from_cuda(cudaLaunchKernel(field_kernels(field).block_dft[log_g],
+                                      dim3(grid_for(b, 128, dev->sms)), dim3(128), args, 0,
+                                      static_cast<cudaStream_t>(stream)));
 }
 
 zkntt_status zkntt_pool_info(size_t *reserved_bytes, size_t *used_bytes) {

@@ -23,8 +23,9 @@ output k by g^-k at the end.
 
 Every arithmetic step runs in the library's kernels (``LibraryOps``): the
 local transform (zkntt_execute), the twiddle and constant scales
-(zkntt_scale_powers) and the butterflies of the G-point transform
-(zkntt_field_op).  The exchange is torch.distributed's all_to_all_single
+(zkntt_scale_powers) and the G-point transforms, one kernel over all columns
+(zkntt_block_dft; with device steps that lack it, radix-2 butterflies on whole
+blocks through zkntt_field_op).  The exchange is torch.distributed's all_to_all_single
 (NCCL between GPUs, no multicast); ``emulate`` runs all G shards in one
 process on one device with the exchange done by copies.  The host computes
 only the per-rank constants (powers of w_n, g, G^-1) with Python integers.
@@ -75,6 +76,10 @@ class LibraryOps:
     def scale_powers(self, x: torch.Tensor, c_mont: int, base_mont: int) -> torch.Tensor:
         from . import scale_powers
         return scale_powers(self.field, x, c_mont, base_mont, out=x)
+
+    def block_dft(self, u: torch.Tensor, log_g: int, inverse: bool) -> torch.Tensor:
+        from . import block_dft
+        return block_dft(self.field, u, log_g, inverse=inverse)
 
     def add(self, a, b):
         from . import field_op
@@ -155,10 +160,15 @@ class ShardedNTT:
         return u
 
     def combine_stage(self, u: torch.Tensor) -> torch.Tensor:
-        """The G-point transforms over the received blocks (radix-2
-        decimation in frequency over whole blocks), then the coset-inverse
-        output scale; returns the local output in output_indices order."""
+        """The G-point transforms over the received blocks (one block-transform
+        kernel for G <= 8, else radix-2 decimation in frequency over whole
+        blocks), then the coset-inverse output scale; returns the local output
+        in output_indices order."""
         F, G, b = self.F, self.G, self.b
+        if 1 < G <= 8 and hasattr(self.ops, "block_dft"):
+            # one kernel: every column's G-point transform, k1-major output
+            out = self.ops.block_dft(u, self.g_bits, self.inverse)
+            return self._coset_inverse_scale(out)
         v = [u[r * b:(r + 1) * b] for r in range(G)]
         wG = F.root(self.g_bits, self.inverse) if G > 1 else 1
         h = G >> 1
@@ -175,6 +185,11 @@ class ShardedNTT:
             h >>= 1
         # position p holds frequency rev(p): reorder to k1-major
         out = torch.cat([v[_rev(k1, self.g_bits)] for k1 in range(G)], dim=0)
+        return self._coset_inverse_scale(out)
+
+    def _coset_inverse_scale(self, out: torch.Tensor) -> torch.Tensor:
+        """Output k times g^-k (coset inverse only); out is k1-major."""
+        F, G, b = self.F, self.G, self.b
         if self.shift is not None and self.inverse:
             ginv = pow(self.shift, -1, F.r)
             for k1 in range(G):

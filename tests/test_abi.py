@@ -82,6 +82,9 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.zkntt_scale_powers(0, None, None, 4, None, one, None) == N.EINVAL
     assert lib.zkntt_scale_powers(9, None, None, 4, one, one, None) == N.EINVAL
     assert lib.zkntt_scale_powers(0, None, None, 0, one, one, None) == N.OK    # empty: no-op
+    assert lib.zkntt_block_dft(0, 4, 8, None, None, 0, None) == N.EINVAL      # G = 16
+    assert lib.zkntt_block_dft(0, 0, 8, None, None, 0, None) == N.EINVAL
+    assert lib.zkntt_block_dft(0, 2, 0, None, None, 0, None) == N.OK          # empty: no-op
 
 
 def test_field_info_without_gpu(lib):

@@ -77,3 +77,23 @@ def test_scale_powers_argument_errors():
         zk.scale_powers(F.name, x, F.r, 1)      # c not canonical
     with pytest.raises(ZkNttError):
         zk.scale_powers(F.name, x, 1, F.r + 5)  # base not canonical
+
+
+@pytest.mark.parametrize("F", FIELDS, ids=lambda f: f.name)
+@pytest.mark.parametrize("log_g", [1, 2, 3])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_block_dft_matches_its_definition(F, log_g, inverse):
+    """zkntt_block_dft against the definition, out[k b + i] = sum_r
+    x[r b + i] w^(r k) with w of order G (inverse: w^-1), in place too."""
+    import paper_2509_22684_gb300 as zk
+    G, b = 1 << log_g, 1000
+    X = uniform_elements(F.r, G * b, 41 + log_g)
+    vals = ref.from_mont_limbs(F, X)
+    w = F.root(log_g, inverse)
+    want = ref.to_mont_limbs(F, [sum(vals[r * b + i] * pow(w, r * k, F.r) for r in range(G)) % F.r
+                                 for k in range(G) for i in range(b)])
+    x = to_dev(X)
+    got = to_host(zk.block_dft(F.name, x, log_g, inverse=inverse))
+    assert np.array_equal(got, want), first_mismatch(got, want)
+    zk.block_dft(F.name, x, log_g, inverse=inverse, out=x)
+    assert np.array_equal(to_host(x), want)

@@ -50,6 +50,20 @@ class OracleOps:
         return self._tensor([(u - v) % self.F.r for u, v in zip(self._vals(a), self._vals(b))])
 
 
+class OracleOpsBlock(OracleOps):
+    """As OracleOps, with the fused G-point step stated from its definition:
+    out[k b + i] = sum_r u[r b + i] w^(r k), w of order G."""
+
+    def block_dft(self, u, log_g, inverse):
+        F, G = self.F, 1 << log_g
+        vals = self._vals(u)
+        b = len(vals) // G
+        w = F.root(log_g, inverse)
+        out = [sum(vals[r * b + i] * pow(w, r * k, F.r) for r in range(G)) % F.r
+               for k in range(G) for i in range(b)]
+        return self._tensor(out)
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
@@ -60,7 +74,7 @@ def _kind_args(F, kind):
     return kind.endswith("intt"), (F.to_mont(F.g) if kind.startswith("coset") else None)
 
 
-def _worker(rank, world, port, field, L, kinds, out):
+def _worker(rank, world, port, field, L, kinds, out, block=False):
     import torch.distributed as dist
     from paper_2509_22684_gb300.sharded import ShardedNTT, scatter_input
     os.environ["MASTER_ADDR"] = "127.0.0.1"
@@ -71,7 +85,8 @@ def _worker(rank, world, port, field, L, kinds, out):
     x = scatter_input(torch.from_numpy(X.view(np.int32).copy()), world)[rank]
     for kind in kinds:
         inverse, shift = _kind_args(F, kind)
-        sh = ShardedNTT(field, L, world, rank, inverse=inverse, coset_shift=shift, ops=OracleOps(F))
+        ops = OracleOpsBlock(F) if block else OracleOps(F)
+        sh = ShardedNTT(field, L, world, rank, inverse=inverse, coset_shift=shift, ops=ops)
         assert torch.equal(sh.input_indices(), torch.arange(rank, 1 << L, world))
         y = sh.execute(x)
         out[(rank, kind)] = (y.numpy().tobytes(), sh.output_indices().numpy().tobytes())
@@ -79,9 +94,10 @@ def _worker(rank, world, port, field, L, kinds, out):
     dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("block", [False, True], ids=["butterflies", "block_step"])
 @pytest.mark.parametrize("world,field,L", [(2, "bls12_381_fr", 6), (4, "bn254_fr", 6),
                                            (4, "bls12_381_fr", 7), (2, "bn254_fr", 2)])
-def test_sharded_transform_over_gloo_ranks_equals_the_oracle(world, field, L):
+def test_sharded_transform_over_gloo_ranks_equals_the_oracle(world, field, L, block):
     from paper_2509_22684_gb300 import build
     from paper_2509_22684_gb300.sharded import gather_output
     build.build()   # the ranks read the field constants through the library
@@ -90,7 +106,7 @@ def test_sharded_transform_over_gloo_ranks_equals_the_oracle(world, field, L):
     ctx = mp.get_context("spawn")
     mgr = ctx.Manager()
     out = mgr.dict()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, field, L, kinds, out))
+    procs = [ctx.Process(target=_worker, args=(r, world, port, field, L, kinds, out, block))
              for r in range(world)]
     for p in procs:
         p.start()
