@@ -76,7 +76,10 @@ __global__ void __launch_bounds__(BATCH_THREADS, BATCH_MIN_BLOCKS)
         const uint32_t nt = pass_threads_for(sg.a.K, sg.a.log_cols, 5);
         // (without the shared-twiddle pairing: at this kernel's 64-register
         // budget it adds spills)
-        run_tile<F, 1, false, false, false>(sg.a, smem, tile, nt < BATCH_THREADS ? nt : BATCH_THREADS);
+#ifndef ZKNTT_BATCH_PAIR
+#define ZKNTT_BATCH_PAIR 0
+#endif
+        run_tile<F, 1, false, false, ZKNTT_BATCH_PAIR>(sg.a, smem, tile, nt < BATCH_THREADS ? nt : BATCH_THREADS);
         // run_tile ends with a block barrier: every store of the tile is issued
         if (threadIdx.x == 0) {
             __threadfence();

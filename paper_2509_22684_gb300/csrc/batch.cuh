@@ -28,7 +28,10 @@ namespace zkntt {
 constexpr int BATCH_MAX_SEGMENTS = 160;
 constexpr uint32_t BATCH_THREADS = 256;
 // blocks per SM the register budget is compiled for (64 registers a thread)
-constexpr int BATCH_MIN_BLOCKS = 4;
+#ifndef ZKNTT_BATCH_MIN_BLOCKS
+#define ZKNTT_BATCH_MIN_BLOCKS 4
+#endif
+constexpr int BATCH_MIN_BLOCKS = ZKNTT_BATCH_MIN_BLOCKS;
 // resident blocks per SM the tile-width policy counts as one wave
 constexpr int BATCH_WAVE_BLOCKS = 3;
 // widest batch tile, log2 elements (32 KiB: four blocks per SM fit in shared memory)
