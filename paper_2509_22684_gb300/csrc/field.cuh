@@ -294,9 +294,36 @@ __device__ __forceinline__ void merge_reduce(uint32_t t[9], const uint64_t Q[8])
 //      the 64-bit addend (shipped)
 //   1: neither row uses the addend (all merging on the ALU pipe)
 //   2: every row uses the addend
+//   4: as 0, with every 64-bit addend formed as the pair {t_j, z_j}, where the
+//      z_j are zero words read from constant memory (kept in registers across
+//      products) rather than a zero-extension of t_j (build-time option)
 #ifndef ZKNTT_MUL_FORM
 #define ZKNTT_MUL_FORM 0
 #endif
+
+#if ZKNTT_MUL_FORM == 4
+// zero words; the product uses them as the high halves of its 64-bit addends
+__constant__ uint32_t kAddendHigh[8];
+#endif
+
+// a b + {hi, lo} as one 32 x 32 + 64-bit multiply-add
+__device__ __forceinline__ uint64_t mad_wide_pair(uint32_t a, uint32_t b, uint32_t lo, uint32_t hi) {
+    uint64_t r;
+    asm("{\n\t.reg .u64 c;\n\tmov.b64 c, {%3, %4};\n\tmad.wide.u32 %0, %1, %2, c;\n\t}"
+        : "=l"(r)
+        : "r"(a), "r"(b), "r"(lo), "r"(hi));
+    return r;
+}
+
+// a b + t (64-bit result) in the addend rows of the product
+__device__ __forceinline__ uint64_t addend_mad(uint32_t a, uint32_t b, uint32_t t, uint32_t zh) {
+#if ZKNTT_MUL_FORM == 4
+    return mad_wide_pair(a, b, t, zh);
+#else
+    (void)zh;
+    return uint64_t(a) * b + t;
+#endif
+}
 
 // ---------------------------------------------------------------------------
 // Form 3 (build-time option, not the default): one level of Karatsuba for the
@@ -493,16 +520,22 @@ __device__ __forceinline__ void mul(uint32_t r[8], const uint32_t a[8], const ui
 #pragma unroll
     for (int i = 0; i < 8; i++) bb[i] = b[i];
     uint32_t t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    constexpr bool rows0 = ZKNTT_MUL_FORM == 0 || ZKNTT_MUL_FORM == 4;
+    uint32_t zh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#if ZKNTT_MUL_FORM == 4
+#pragma unroll
+    for (int j = 0; j < 8; j++) zh[j] = kAddendHigh[j];
+#endif
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         uint64_t X[8];
-        if (ZKNTT_MUL_FORM == 0 && i == 0) {
+        if (rows0 && i == 0) {
 #pragma unroll
             for (int j = 0; j < 8; j++) X[j] = uint64_t(a[j]) * bb[0];
             merge_first_row(t, X);
-        } else if (ZKNTT_MUL_FORM == 2 || (ZKNTT_MUL_FORM == 0 && i == 7)) {
+        } else if (ZKNTT_MUL_FORM == 2 || (rows0 && i == 7)) {
 #pragma unroll
-            for (int j = 0; j < 8; j++) X[j] = uint64_t(a[j]) * bb[i] + t[j];
+            for (int j = 0; j < 8; j++) X[j] = addend_mad(a[j], bb[i], t[j], zh[j]);
             merge_addend_row(t, X);
         } else {
 #pragma unroll
@@ -523,7 +556,10 @@ __device__ __forceinline__ void mul(uint32_t r[8], const uint32_t a[8], const ui
             t[8] = 0;
         } else {
 #pragma unroll
-            for (int j = 0; j < 8; j++) X[j] = uint64_t(m) * P[j] + t[j];
+            for (int j = 0; j < 8; j++)
+                // (limbs 1 and 2^32 - 1 stay plain C: the compiler forms them without multiplies)
+                X[j] = (P[j] == 1u || P[j] == 0xffffffffu) ? uint64_t(m) * P[j] + t[j]
+                                                           : addend_mad(m, P[j], t[j], zh[j]);
             if constexpr (F::P0 == 0xf0000001u) {
                 // r_0 = 2^32 - 2^28 + 1: the low word of m r_0 + t_0 is zero by
                 // the choice of m, and its high word is m - (m >> 4) + carry(m + t_0)

@@ -88,6 +88,11 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
 
+// the same with the shared-memory destination as a 32-bit shared address
+__device__ __forceinline__ void cp_async16_sa(uint32_t s, const void *gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
@@ -180,8 +185,54 @@ __device__ __forceinline__ void issue_tile_load(const PassArgs &a, uint4 *smem, 
     const uint32_t N = 1u << K, C = 1u << lc, CN = C << K;
     uint4 *s_lo = smem, *s_hi = smem + CN;
     const uint32_t tid = threadIdx.x;
+    if (tid >= nthreads) return;
+    if (CN >= 64 && (nthreads & 15u) == 0 && (nthreads & (nthreads - 1u)) == 0 && nthreads <= 2 * CN) {
+        // Every thread makes 2 C N / nthreads copies of one half (the lane's
+        // bit 3) of elements e0, e0 + E, e0 + 2E, ... (E = nthreads / 2); in
+        // a strided pass they share a column and step by a fixed row count,
+        // so the source address steps by a fixed stride and only the shared
+        // slot is formed per copy.
+        const uint32_t half = (tid >> 3) & 1u;
+        const uint32_t e0 = (tid & 7u) | ((tid >> 4) << 3);
+        const uint32_t E = nthreads >> 1, iters = (2 * CN) / nthreads;
+        const uint32_t sbase =
+            static_cast<uint32_t>(__cvta_generic_to_shared(half ? s_hi : s_lo));
+        if (!a.last) {
+            const uint32_t cc = e0 & (C - 1), dstep = E >> lc;
+            uint32_t d = e0 >> lc;
+            const uint4 *src = a.in + 2 * tile_src(a, tile, d, cc) + half;
+            const size_t sstep = size_t(2 * dstep) << a.lo_bits;
+            if ((dstep & 15u) == 0) {
+                // rows d, d + dstep, ... agree in their low four bits, so they
+                // share the swizzle term and their slots step by dstep too
+                uint32_t sa = sbase + 16u * smem_slot(cc, d, K, lc);
+                for (uint32_t k = 0; k < iters; k++, sa += 16u * dstep, src += sstep)
+                    cp_async16_sa(sa, src);
+            } else {
+                for (uint32_t k = 0; k < iters; k++, d += dstep, src += sstep)
+                    cp_async16_sa(sbase + 16u * smem_slot(cc, d, K, lc), src);
+            }
+        } else if (E < N) {
+            // last pass, rows fastest: N / E copies in one column (rows e0,
+            // e0 + E, ...; e0 < E), then the next column
+            const uint32_t per = N / E;
+            for (uint32_t cc = 0; cc < C; cc++) {
+                const uint4 *row = a.in + 2 * tile_src(a, tile, 0, cc) + half;
+                for (uint32_t j = 0, d = e0; j < per; j++, d += E)
+                    cp_async16_sa(sbase + 16u * smem_slot(cc, d, K, lc), row + 2 * d);
+            }
+        } else {
+            uint32_t e = e0;
+            for (uint32_t k = 0; k < iters; k++, e += E) {
+                const uint32_t d = e & (N - 1), cc = e >> K;
+                cp_async16_sa(sbase + 16u * smem_slot(cc, d, K, lc),
+                              a.in + 2 * tile_src(a, tile, d, cc) + half);
+            }
+        }
+        return;
+    }
     const bool grouped = CN >= 8;
-    for (uint32_t u = tid; tid < nthreads && u < 2 * CN; u += nthreads) {
+    for (uint32_t u = tid; u < 2 * CN; u += nthreads) {
         const uint32_t e = grouped ? ((u & 7u) | ((u >> 4) << 3)) : (u >> 1);
         const uint32_t half = grouped ? ((u >> 3) & 1u) : (u & 1u);
         uint32_t d, cc;
@@ -399,8 +450,9 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
             const uint32_t cc = qd & (C - 1);
             const uint32_t d0 = (qd >> lc) << 2;
             uint32_t x0[8], x1[8], x2[8], x3[8], t[8];
-            const uint32_t s0 = smem_slot(cc, d0, K, lc), s1 = smem_slot(cc, d0 + 1, K, lc);
-            const uint32_t s2 = smem_slot(cc, d0 + 2, K, lc), s3 = smem_slot(cc, d0 + 3, K, lc);
+            // rows d0 + i (d0 a multiple of 4) share the swizzle term: their
+            // slots are the first one's with i in the low two bits
+            const uint32_t s0 = smem_slot(cc, d0, K, lc), s1 = s0 ^ 1u, s2 = s0 ^ 2u, s3 = s0 ^ 3u;
             lds_elem(x0, s_lo, s_hi, s0);
             lds_elem(x1, s_lo, s_hi, s1);
             lds_elem(x2, s_lo, s_hi, s2);
