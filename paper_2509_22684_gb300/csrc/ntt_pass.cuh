@@ -354,7 +354,7 @@ __device__ __forceinline__ void run_tile(const PassArgs &a, uint4 *smem, uint32_
                 const uint32_t q0b = (q0 + ((C >> 1) << K)) ^ (K >= 3 ? 4u : 0u);
                 uint32_t w[8];
                 ldg_elem(w, ws + 2 * size_t(j));
-#pragma unroll 1
+#pragma unroll
                 for (int q = 0; q < 2; q++) {
                     const uint32_t a0 = q ? q0b : q0;
                     uint32_t x[8], y[8], t[8];
