@@ -52,7 +52,7 @@ typedef enum {
     ZKNTT_ENOMEM = 2,        /* device allocation failed */
     ZKNTT_ECUDA = 3,         /* a CUDA runtime call failed; see zkntt_last_cuda_error */
     ZKNTT_ETIMEOUT = 4,      /* a bounded device-side wait gave up (batch dependency never met) */
-    ZKNTT_EUNSUPPORTED = 5   /* valid request this build does not implement */
+    ZKNTT_EUNSUPPORTED = 5   /* valid request the library does not implement */
 } zkntt_status;
 
 typedef enum {
