@@ -544,9 +544,18 @@ template <> struct PassVariant<7> { static constexpr int ILP = 1, MIN_BLOCKS = 3
 template <class F, int V>
 __global__ void __launch_bounds__(256, PassVariant<V>::MIN_BLOCKS) ntt_pass_kernel(const PassArgs a) {
     extern __shared__ uint4 smem[];
+    // Passes after the first are launched as programmatic dependents of the
+    // pass before, and wait here until that pass has completed and its writes
+    // are visible (launched without that attribute, the wait returns at once).
+    // A block lets the next pass launch when it starts its last tile, so the
+    // next pass's blocks take SM places only as this grid winds down.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (V != 6 || a.pre || a.pw_b) {
-        for (uint32_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x)
+        for (uint32_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
+            if (tile + gridDim.x >= a.num_tiles)
+                asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
             run_tile<F, PassVariant<V>::ILP, false, V == 7>(a, smem, tile, blockDim.x);
+        }
         return;
     }
     // Variant 6: two tile buffers.  The copies of the block's next tile are in
@@ -562,6 +571,7 @@ __global__ void __launch_bounds__(256, PassVariant<V>::MIN_BLOCKS) ntt_pass_kern
     uint32_t cur = 0;
     for (; tile < a.num_tiles; tile += gridDim.x) {
         const uint32_t next = tile + gridDim.x;
+        if (next >= a.num_tiles) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         if (next < a.num_tiles) {
             issue_tile_load(a, smem + (cur ^ 1u) * 2 * CN, next, blockDim.x);
             cp_async_commit();
