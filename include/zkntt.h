@@ -138,7 +138,12 @@ zkntt_status zkntt_plan_describe(zkntt_plan plan, int *num_passes, int digit_bit
  * d_in == d_out (in place) is allowed; partial overlap is EINVAL; a plan of
  * another device than the current one is EINVAL.  Scratch for multi-pass
  * sizes comes from the library's stream-ordered pool (allocated on `stream`,
- * released on `stream`).
+ * released on `stream`).  The passes are enqueued on `stream` in order: the
+ * first after all earlier work on it; the later ones as programmatic
+ * dependents of the pass before (each waits for that pass's completion before
+ * touching memory).  Work the caller enqueues afterwards sees the whole result
+ * unless it is itself a programmatic dependent launch, which must then wait
+ * (griddepcontrol.wait) before reading d_out.
  */
 zkntt_status zkntt_execute(zkntt_plan plan, const void *d_in, void *d_out, void *stream);
 
